@@ -1,0 +1,301 @@
+"""Seeded synthetic inputs shaped like the paper's test cases.
+
+This module holds case recipes only: initial order-parameter and velocity
+fields (the tanh interface profiles of Sec. III and Sec. IV, random
+solenoidal velocity fields, droplet placement) and the nondimensional
+parameter dictionaries. It contains none of the lattice Boltzmann arithmetic;
+both the CUDA path and the CPU oracle take these arrays and build their own
+populations from them.
+
+Every generator is deterministic given its seed. Arrays are numpy float64 with
+the field layout (ny, nx) or (nz, ny, nx) (x fastest) and vectors (d, *field).
+"""
+
+import math
+
+import numpy as np
+
+FAKHARI2017, CHAI2018, HU2019, LIANG2014 = 0, 1, 2, 3
+FAMILIES = (FAKHARI2017, CHAI2018, HU2019, LIANG2014)
+FAMILY_NAMES = {FAKHARI2017: "fakhari2017", CHAI2018: "chai2018",
+                HU2019: "hu2019", LIANG2014: "liang2014"}
+
+DEFAULT_SEED = 20251114
+
+
+def params(**kw):
+    """A complete parameter dictionary (lattice units) with the paper's defaults."""
+    p = dict(dim=2, nx=64, ny=64, nz=1, family=FAKHARI2017, bc_y=0,
+             phi_H=1.0, phi_L=0.0, rho_H=1.0, rho_L=1.0, nu_H=0.1, nu_L=0.1,
+             visc_interp=0, sigma=1e-3, W=4.0, M=0.1, lambda_hybrid=0.9,
+             eta_ch=1.0, gravity=(0.0, 0.0, 0.0), force_density=(0.0, 0.0, 0.0),
+             lundgren_A=0.0, wall_u=(0.0, 0.0), grad_eps=1e-12, freeze_phi=0)
+    p.update(kw)
+    return p
+
+
+def tau_to_nu(tau):
+    return (tau - 0.5) / 3.0
+
+
+def _grid(shape):
+    """Cell-centre coordinates (x, y[, z]) as float64 arrays of the field shape."""
+    axes = [np.arange(n, dtype=np.float64) for n in shape]
+    mesh = np.meshgrid(*axes, indexing="ij")
+    return mesh[::-1]  # x, y[, z]
+
+
+def _tanh_profile(signed_dist, W, phi_H=1.0, phi_L=0.0):
+    """phi = (phi_H+phi_L)/2 + (phi_H-phi_L)/2 tanh(2 d / W), d > 0 inside the heavy phase."""
+    return 0.5 * (phi_H + phi_L) + 0.5 * (phi_H - phi_L) * np.tanh(2.0 * signed_dist / W)
+
+
+# --------------------------------------------------------------------------
+# 2D laminar cases
+# --------------------------------------------------------------------------
+def static_droplet_2d(nx=64, ny=64, R=16.0, W=4.0, family=FAKHARI2017, **kw):
+    """Heavy droplet of radius R at the domain centre, fluid at rest (Sec. III A
+    profile, Eq. init-phi-circle). Defaults: 64x64, R=16, W=4, sigma=1e-3, M=0.1,
+    tau=0.8, density and viscosity ratio 1."""
+    x, y = _grid((ny, nx))
+    r = np.sqrt((x - 0.5 * nx + 0.5) ** 2 + (y - 0.5 * ny + 0.5) ** 2)
+    phi = _tanh_profile(R - r, W)
+    u = np.zeros((2, ny, nx))
+    P = params(dim=2, nx=nx, ny=ny, nz=1, family=family, W=W, sigma=1e-3, M=0.1,
+               nu_H=tau_to_nu(0.8), nu_L=tau_to_nu(0.8))
+    P.update(kw)
+    return P, phi, u
+
+
+def translating_droplet_2d(L0=100, U0=0.02, W=None, family=FAKHARI2017, **kw):
+    """Diagonal translation of a circular droplet, Sec. III A: R = L0/5,
+    U = (U0, U0), sigma = 0.01, M = 0.0013, xi = 0.02 L0 (paper: L0 = 200)."""
+    W = 0.02 * L0 if W is None else float(W)
+    x, y = _grid((L0, L0))
+    r = np.sqrt((x - 0.5 * L0) ** 2 + (y - 0.5 * L0) ** 2)
+    phi = _tanh_profile(L0 / 5.0 - r, W)
+    u = np.stack([np.full((L0, L0), U0), np.full((L0, L0), U0)])
+    P = params(dim=2, nx=L0, ny=L0, family=family, W=W, sigma=0.01, M=0.0013,
+               nu_H=0.1, nu_L=0.1)
+    P.update(kw)
+    return P, phi, u
+
+
+def droplet_in_vortex_2d(nx=100, ny=70, R=14.0, W=4.0, u0=0.02, family=FAKHARI2017, seed=DEFAULT_SEED, **kw):
+    """A droplet off-centre in a periodic Taylor-Green vortex field; a laminar
+    case with a real flow, used for GPU-vs-oracle parity on ragged grids."""
+    rng = np.random.default_rng(seed)
+    x, y = _grid((ny, nx))
+    cx, cy = nx * (0.4 + 0.2 * rng.random()), ny * (0.4 + 0.2 * rng.random())
+    r = np.sqrt((x - cx) ** 2 + (y - cy) ** 2)
+    phi = _tanh_profile(R - r, W)
+    kx, ky = 2 * math.pi / nx, 2 * math.pi / ny
+    u = np.stack([u0 * np.sin(kx * x) * np.cos(ky * y),
+                  -u0 * (kx / ky) * np.cos(kx * x) * np.sin(ky * y)])
+    P = params(dim=2, nx=nx, ny=ny, family=family, W=W, sigma=5e-3, M=0.05,
+               rho_H=1.0, rho_L=1.0, nu_H=tau_to_nu(0.8), nu_L=tau_to_nu(0.8))
+    P.update(kw)
+    return P, phi, u
+
+
+def rayleigh_taylor_2d(nx=256, ny=1024, At=0.5, Re=3000.0, Pe=1000.0, W=5.0,
+                       amp=0.1, family=FAKHARI2017, **kw):
+    """Rayleigh-Taylor instability, Sec. III C, with the heavier fluid above the
+    perturbed interface y_t = 2 L0 + amp L0 cos(2 pi x / L0), L0 = nx.
+    sqrt(g L0) = 0.04, sigma = 5e-5; At, Re and Pe fix rho_H/rho_L, nu and M.
+    Periodic in x, no-slip walls in y."""
+    L0 = nx
+    g = 0.04 ** 2 / L0
+    rho_L = 1.0
+    rho_H = rho_L * (1 + At) / (1 - At)
+    nu = L0 * math.sqrt(At * g * L0 / (1 + At)) / Re
+    M = L0 * math.sqrt(g * L0) / Pe
+    x, y = _grid((ny, nx))
+    yt = 0.5 * ny + amp * L0 * np.cos(2 * math.pi * (x + 0.5) / L0)
+    phi = _tanh_profile((y + 0.5) - yt, W)
+    u = np.zeros((2, ny, nx))
+    P = params(dim=2, nx=nx, ny=ny, family=family, bc_y=1, rho_H=rho_H, rho_L=rho_L,
+               nu_H=nu, nu_L=nu, sigma=5e-5, W=W, M=M, gravity=(0.0, -g, 0.0))
+    P.update(kw)
+    return P, phi, u
+
+
+def layered_poiseuille_2d(nx=10, ny=100, uc=1e-3, ratio=1000.0, W=4.0, M=0.1,
+                          sigma=1e-3, nu_H=0.1, family=FAKHARI2017, **kw):
+    """Stratified Poiseuille flow, Sec. III D: heavy fluid in the lower half,
+    walls at y = -1/2 and ny - 1/2 (H = ny/2), force density
+    G_x = u_c (mu_H + mu_L)/H^2, phase field frozen, linear dynamic-viscosity
+    interpolation (Eq. mu_linear). ``ratio`` is both rho_H/rho_L and mu_H/mu_L."""
+    H = ny / 2.0
+    rho_H, rho_L = 1.0, 1.0 / ratio
+    mu_H = rho_H * nu_H
+    mu_L = mu_H / ratio
+    nu_L = mu_L / rho_L
+    Gx = uc * (mu_H + mu_L) / H ** 2
+    x, y = _grid((ny, nx))
+    phi = _tanh_profile(H - (y + 0.5), W)
+    u = np.zeros((2, ny, nx))
+    P = params(dim=2, nx=nx, ny=ny, family=family, bc_y=1, rho_H=rho_H, rho_L=rho_L,
+               nu_H=nu_H, nu_L=nu_L, visc_interp=1, sigma=sigma, W=W, M=M,
+               force_density=(Gx, 0.0, 0.0), freeze_phi=1)
+    P.update(kw)
+    return P, phi, u
+
+
+# --------------------------------------------------------------------------
+# 3D cases
+# --------------------------------------------------------------------------
+def solenoidal_field(shape, k0=4.0, u_rms=0.04, nmodes=48, seed=DEFAULT_SEED, kmax=8):
+    """Random-phase divergence-free velocity field on a periodic box.
+
+    u(x) = sum_m a_m q_m cos(k_m . x + theta_m) with integer wave vectors k_m
+    (units of 2 pi / n), q_m a unit vector normal to k_m, amplitudes drawn so
+    the shell energy follows E(k) ~ k^4 exp(-2 k^2 / k0^2); scaled to u_rms.
+    Each term is divergence free, so the sum is."""
+    rng = np.random.default_rng(seed)
+    d = len(shape)
+    n = shape[::-1]  # nx, ny, nz
+    modes = []
+    while len(modes) < nmodes:
+        k = rng.integers(-kmax, kmax + 1, size=d)
+        kk = math.sqrt(float(np.sum(k * k)))
+        if kk < 1.0:
+            continue
+        modes.append(k)
+    x = _grid(shape)
+    u = np.zeros((d,) + tuple(shape))
+    for k in modes:
+        kvec = np.array([2 * math.pi * k[i] / n[i] for i in range(d)])
+        kk = np.linalg.norm(kvec)
+        r = rng.normal(size=d)
+        q = r - np.dot(r, kvec) / kk ** 2 * kvec
+        q /= np.linalg.norm(q)
+        kmag = math.sqrt(float(np.sum(np.asarray(k, dtype=float) ** 2)))
+        amp = math.sqrt(kmag ** 4 * math.exp(-2 * kmag ** 2 / k0 ** 2)) / kmag
+        theta = rng.uniform(0, 2 * math.pi)
+        arg = sum(kvec[i] * x[i] for i in range(d)) + theta
+        c = np.cos(arg)
+        for i in range(d):
+            u[i] += amp * q[i] * c
+    rms = math.sqrt(float(np.mean(np.sum(u * u, axis=0))) / d)
+    return u * (u_rms / rms)
+
+
+def place_droplets(n, count, R, W, seed=DEFAULT_SEED, max_tries=200000):
+    """Uniform-random droplet centres in a periodic cube of side n with periodic
+    separation at least 2R + 4W (rejection sampling)."""
+    rng = np.random.default_rng(seed)
+    dmin = 2 * R + 4 * W
+    centres = []
+    tries = 0
+    while len(centres) < count:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("could not place droplets")
+        c = rng.uniform(0, n, size=3)
+        ok = True
+        for o in centres:
+            dd = np.abs(c - o)
+            dd = np.minimum(dd, n - dd)
+            if np.sum(dd * dd) < dmin * dmin:
+                ok = False
+                break
+        if ok:
+            centres.append(c)
+    return np.array(centres)
+
+
+def droplet_field(n, centres, R, W, dtype=np.float64):
+    """phi of heavy droplets (Eq. init-phi-droplet-3D profile per droplet) in a
+    periodic cube; each droplet is written in a box of half-width R + 5W and
+    combined by maximum (droplets are separated by at least 4W)."""
+    phi = np.zeros((n, n, n), dtype=dtype)
+    h = int(math.ceil(R + 5 * W))
+    off = np.arange(-h, h + 1)
+    for c in centres:
+        ic = np.floor(c).astype(int)
+        ix = (ic[0] + off) % n
+        iy = (ic[1] + off) % n
+        iz = (ic[2] + off) % n
+        dx = (ic[0] + off + 0.5) - c[0]
+        dy = (ic[1] + off + 0.5) - c[1]
+        dz = (ic[2] + off + 0.5) - c[2]
+        r = np.sqrt(dz[:, None, None] ** 2 + dy[None, :, None] ** 2 + dx[None, None, :] ** 2)
+        blob = _tanh_profile(R - r, W).astype(dtype)
+        sub = phi[np.ix_(iz, iy, ix)]
+        phi[np.ix_(iz, iy, ix)] = np.maximum(sub, blob)
+    return phi
+
+
+def hit_droplets_3d(n=512, count=200, R=16.0, W=4.0, We=5.0, u_rms=0.04, nu=0.006,
+                    M=0.01, lundgren_A=1e-4, seed=DEFAULT_SEED, family=FAKHARI2017,
+                    dtype=np.float64, with_velocity=True, **kw):
+    """Droplet-laden forced isotropic turbulence, Sec. IV: periodic cube,
+    density ratio 1, sigma = rho_H u_rms^2 (2R) / We (Sec. IV definition of We),
+    linear forcing coefficient A (the paper's stochastic forcing is replaced by
+    linear forcing F = A rho u). The velocity is a random solenoidal field."""
+    centres = place_droplets(n, count, R, W, seed=seed)
+    phi = droplet_field(n, centres, R, W, dtype=dtype)
+    u = None
+    if with_velocity:
+        u = solenoidal_field((n, n, n), u_rms=u_rms, seed=seed + 1).astype(dtype)
+    sigma = 1.0 * u_rms ** 2 * (2 * R) / We
+    P = params(dim=3, nx=n, ny=n, nz=n, family=family, rho_H=1.0, rho_L=1.0,
+               nu_H=nu, nu_L=nu, sigma=sigma, W=W, M=M, lundgren_A=lundgren_A)
+    P.update(kw)
+    return P, phi, u, centres
+
+
+def droplet_in_tgv_3d(n=32, R=6.0, W=4.0, u0=0.02, family=FAKHARI2017, nx=None, ny=None, nz=None, **kw):
+    """Droplet of radius R at the centre of a Taylor-Green vortex,
+    u = u0 (sin kx cos ky cos kz, -cos kx sin ky cos kz, 0)."""
+    nx = nx or n
+    ny = ny or n
+    nz = nz or n
+    x, y, z = _grid((nz, ny, nx))
+    r = np.sqrt((x - 0.5 * nx) ** 2 + (y - 0.5 * ny) ** 2 + (z - 0.5 * nz) ** 2)
+    phi = _tanh_profile(R - r, W)
+    kx, ky, kz = 2 * math.pi / nx, 2 * math.pi / ny, 2 * math.pi / nz
+    u = np.stack([u0 * np.sin(kx * x) * np.cos(ky * y) * np.cos(kz * z),
+                  -u0 * (kx / ky) * np.cos(kx * x) * np.sin(ky * y) * np.cos(kz * z),
+                  np.zeros_like(x)])
+    P = params(dim=3, nx=nx, ny=ny, nz=nz, family=family, W=W, M=0.1, sigma=1e-3,
+               nu_H=tau_to_nu(0.8), nu_L=tau_to_nu(0.8))
+    P.update(kw)
+    return P, phi, u
+
+
+# --------------------------------------------------------------------------
+# Batched 2D sweep: droplets in shear
+# --------------------------------------------------------------------------
+def shear_instance(L, family, Ca, M, W, Uw=0.02, tau=0.8):
+    """Droplet (R = L/8) at the centre of an L x L channel between walls moving
+    at -Uw (bottom) and +Uw (top); sigma = rho nu gamma_dot R / Ca with
+    gamma_dot = 2 Uw / L."""
+    nu = tau_to_nu(tau)
+    R = L / 8.0
+    gdot = 2 * Uw / L
+    sigma = 1.0 * nu * gdot * R / Ca
+    x, y = _grid((L, L))
+    r = np.sqrt((x - 0.5 * L + 0.5) ** 2 + (y - 0.5 * L + 0.5) ** 2)
+    phi = _tanh_profile(R - r, W)
+    ywall = (y + 0.5) / L * 2.0 - 1.0
+    u = np.stack([Uw * ywall, np.zeros_like(x)])
+    P = params(dim=2, nx=L, ny=L, family=family, bc_y=2, wall_u=(-Uw, Uw), sigma=sigma,
+               W=float(W), M=M, nu_H=nu, nu_L=nu)
+    return P, phi, u
+
+
+def batched_shear_sweep(count=512, sizes=(64, 128, 256, 512), seed=DEFAULT_SEED):
+    """``count`` instances with L uniform in ``sizes``, Ca ~ U[0.05, 0.5],
+    M ~ U[0.01, 0.2], W uniform in {3, 4, 5}, family uniform over the four."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        L = int(rng.choice(sizes))
+        fam = int(rng.integers(0, 4))
+        Ca = float(rng.uniform(0.05, 0.5))
+        M = float(rng.uniform(0.01, 0.2))
+        W = int(rng.choice([3, 4, 5]))
+        out.append(dict(L=L, family=fam, Ca=Ca, M=M, W=W))
+    return out
