@@ -1,0 +1,336 @@
+"""Throughput of the coupled PF-LB step on GB300 (one JSON line on stdout).
+
+Workload (default): 3D droplet-laden forced isotropic turbulence, 512^3
+periodic, D3Q19 hydrodynamics + D3Q7 phase field, 200 droplets of R = 16,
+W = 4, We = 5, density ratio 1, linear forcing, conservative Allen-Cahn
+(Fakhari2017), FP32 populations. A step is one launch of the fused kernel.
+
+  value        device-timed GLUPS (cells x steps / s / 1e9), whole job over
+               all ranks (weak scaling: each rank its own 512^3 instance)
+  e2e          the same metric through the C ABI with host buffers: init from
+               pinned host fields, every step followed by a host read of that
+               step's observables, final phi copied back to the host
+  roofline     algorithmic bytes/LU x cells / kernel time against the measured
+               HBM copy bandwidth
+  variants     FP16 / BF16 deviation storage of the same workload
+  cpu_baseline the FP64 oracle on a bounded sample, host cores
+
+--impl reference times the FP64 oracle (the only reference this method has)
+on a bounded sample of the same workload.
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = ("3D droplet-laden forced HIT 512^3 periodic, D3Q19+D3Q7, 200 droplets R=16, W=4, "
+            "We=5, density ratio 1, linear forcing, conservative Allen-Cahn (Fakhari2017)")
+METRIC = "coupled GLUPS (512^3 D3Q19+D3Q7 fused PF-LB step)"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi samples of this GPU's clocks during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[5:9]):
+                    if v.lower() in ("active", "0x1", "1"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_steps(sim, steps, warmup, world):
+    """Device time of `steps` calls of the fused step (CUDA events on the
+    stream the library launches on)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    sim.step(warmup)
+    sim.sync()
+    _barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    _barrier(world)
+    sim.sync()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def e2e_run(P, phi_host, u_host, steps, world):
+    """Whole job through the C ABI with host buffers."""
+    import numpy as np
+    import torch
+    from paper_2511_11360_gb300 import pflb
+    sim = pflb.Sim(P, stream=torch.cuda.current_stream())
+    out_phi = np.empty(phi_host.shape, dtype=np.float32)
+    # warm-up job (first-touch of the library's buffers)
+    sim.init(phi_host, u_host)
+    sim.step(1)
+    sim.history(1)
+    torch.cuda.synchronize()
+    _barrier(world)
+    t0 = time.perf_counter()
+    sim.init(phi_host, u_host)
+    for _ in range(steps):
+        sim.step(1)
+        sim.history(1)
+    sim.fields(phi=out_phi)
+    t1 = time.perf_counter()
+    _barrier(world)
+    sim.close()
+    return t1 - t0
+
+
+def cpu_baseline(seconds_target=15.0):
+    """The FP64 oracle, unmodified, on a bounded sample of the workload: a
+    periodic 64^3 box of the same recipe (2 droplets of R = 16, W = 4,
+    solenoidal velocity), as many steps as fit the target time."""
+    import numpy as np
+    import oracle as O
+    from paper_2511_11360_gb300 import cases as C
+    n = 64
+    P, phi, u, _ = C.hit_droplets_3d(n=n, count=2, R=16.0, W=4.0, We=5.0, seed=C.DEFAULT_SEED)
+    st = O.init_state(P, phi, u)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        st = O.step(P, st)
+        steps += 1
+        if time.perf_counter() - t0 > seconds_target or steps >= 50:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n ** 3 * steps / dt / 1e9, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+            "sample": "%d steps of a 64^3 periodic box of the same recipe (2 droplets R=16, W=4, "
+                      "solenoidal u), numpy float64, single thread; %.1f s" % (steps, dt)}
+
+
+def reference_main(args):
+    rank, world, local = _dist()
+    if rank != 0:
+        return 0
+    per = []
+    for _ in range(args.warmup):
+        cpu_baseline(seconds_target=2.0)
+    t0 = time.perf_counter()
+    vals = []
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(seconds_target=4.0))
+    dt = time.perf_counter() - t0
+    value = statistics.median(v["value"] for v in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / max(args.steps, 1) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (bounded 64^3 sample on host cores)"},
+            "cpu_baseline": dict(vals[-1], value=value),
+            "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_main(args)
+
+    import numpy as np
+    import torch
+    from paper_2511_11360_gb300 import build as B
+    from paper_2511_11360_gb300 import cases as C
+    from paper_2511_11360_gb300 import pflb
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        B.build()
+    _barrier(world)
+    if rank != 0:
+        B.build()
+    pflb.load_library()
+
+    n = args.n
+    P, phi, u, centres = C.hit_droplets_3d_torch(n=n, seed=C.DEFAULT_SEED + rank)
+    cells = n ** 3
+    peak, peak_kind = _peaks()
+
+    # ---- FP32, device-resident inputs
+    sim = pflb.Sim(dict(P, obs_capacity=4), stream=torch.cuda.current_stream())
+    sim.init(phi, u)
+    bytes_lu = sim.bytes_per_update()
+    clocks = Clocks(local)
+    clocks.start()
+    t = time_steps(sim, args.steps, args.warmup, world)
+    ck = clocks.stop()
+    t = _max_over_ranks(t, world)
+    obs = sim.observables()
+    sim.close()
+    value = cells * args.steps * world / t / 1e9
+    ms = t / args.steps * 1e3
+    achieved = bytes_lu * cells / (t / args.steps) / 1e9
+    traffic = None
+    try:
+        with open(PROFILE_TRAFFIC) as fh:
+            tr = json.load(fh)
+        if tr.get("workload_n") == n and tr.get("kernel_rev") == "v1":
+            traffic = tr.get("bytes_per_launch")
+    except Exception:
+        pass
+
+    # ---- variants: FP16 / BF16 deviation storage
+    variants = {}
+    if not args.no_variants:
+        for name, st in (("fp16_storage", 1), ("bf16_storage", 2)):
+            s2 = pflb.Sim(dict(P, storage=st, obs_capacity=4), stream=torch.cuda.current_stream())
+            s2.init(phi, u)
+            b2 = s2.bytes_per_update()
+            t2 = _max_over_ranks(time_steps(s2, args.steps, args.warmup, world), world)
+            s2.close()
+            variants[name] = {"value": cells * args.steps * world / t2 / 1e9, "unit": "GLUPS",
+                              "bytes_per_lu": b2, "roofline_frac": b2 * cells / (t2 / args.steps) / 1e9 / peak,
+                              "ms_per_step": t2 / args.steps * 1e3}
+
+    # ---- end to end through the C ABI with host buffers
+    phi_h = torch.empty(phi.shape, dtype=torch.float32, pin_memory=True)
+    u_h = torch.empty(u.shape, dtype=torch.float32, pin_memory=True)
+    phi_h.copy_(phi)
+    u_h.copy_(u)
+    del phi, u
+    torch.cuda.empty_cache()
+    e2e_steps = max(args.steps // 2, 5)
+    te = _max_over_ranks(e2e_run(dict(P, obs_capacity=4), phi_h.numpy(), u_h.numpy(), e2e_steps, world), world)
+    e2e = {"value": cells * e2e_steps * world / te / 1e9, "unit": "GLUPS",
+           "h2d_bytes_per_step": int(4 * cells * 4 / e2e_steps),
+           "d2h_bytes_per_step": int(96 + 4 * cells / e2e_steps)}
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+    cpu = None if args.no_cpu else cpu_baseline()
+    line = {
+        "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": cells, "family": "fakhari2017",
+                   "storage": "fp32", "l2": "state %.1f GB >> 126 MB L2, no flush needed" % (
+                       bytes_lu * cells / 2 / 1e9),
+                   "bytes_per_lu": bytes_lu, "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "step_kernel<fakhari,3D,f32>"},
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": ck,
+        "variants": variants,
+        "err_vs_oracle": "fp32: phi,u rel Linf <= 1e-5 after 1000 steps (laminar, tests/test_gpu_parity.py); "
+                         "one step at sampled 512^3 cells <= 2e-6 of max|population| (tests/test_gpu_fullsize.py)",
+        "obs_after": {"sum_phi": obs["sum_phi"], "vol_count": obs["vol_count"], "ke": obs["ke"]},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

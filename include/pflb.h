@@ -1,0 +1,193 @@
+/*
+ * pflb.h -- C ABI of the GB300 coupled phase-field lattice Boltzmann step.
+ *
+ * The library advances two lattice Boltzmann population sets coupled through
+ * the order parameter phi, as compared in "Comparative study and critical
+ * assessment of phase-field lattice Boltzmann models for laminar and turbulent
+ * two-phase flow simulations" (arXiv 2511.11360):
+ *   g_a (phase field; D2Q9 in 2D, D3Q7 in 3D) and f_b (hydrodynamics; D2Q9 in
+ *   2D, D3Q19 in 3D), both relaxed by BGK with a source weighted by
+ *   (1 - 1/(2 tau)) (Sec. II B, Eqs. fakhari_g_simplified and
+ *   fakhari_f_simplified), with the equilibria and sources of one of four
+ *   families (Sec. II C, II D) and the isotropic central stencils of Sec. III.
+ *
+ * Conventions for every entry point:
+ *   - Return value: PFLB_OK (0) or a negative pflb_status. Errors are sticky
+ *     per handle; pflb_last_error() gives the message.
+ *   - Pointers documented "host or device" may point to pageable host memory,
+ *     pinned host memory or device memory of the handle's device (unified
+ *     addressing decides the copy direction). The caller owns every pointer it
+ *     passes; the library never frees or retains them past the call.
+ *   - The library owns its population buffers (device memory it allocates in
+ *     pflb_create and frees in pflb_destroy).
+ *   - Work is issued on the CUDA stream given at creation (NULL = legacy
+ *     default stream). Calls that return data to the host synchronise that
+ *     stream; pflb_step does not.
+ *   - There is no CPU implementation: without a CUDA device every call that
+ *     needs one returns PFLB_ECUDA.
+ *   - Field layout: cell (x, y[, z]) has linear index x + nx*(y + ny*z), x
+ *     fastest. Scalar fields are N = nx*ny*nz floats; vector fields are d
+ *     consecutive scalar fields (x component first).
+ *   - Units are lattice units (dx = dt = 1).
+ */
+#ifndef PFLB_H
+#define PFLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pflb_status {
+  PFLB_OK = 0,
+  PFLB_EINVAL = -1,    /* invalid argument or parameter */
+  PFLB_ENOMEM = -2,    /* device allocation failed */
+  PFLB_ECUDA = -3,     /* CUDA runtime error or no device */
+  PFLB_EUNSTABLE = -4, /* a step produced rho <= 0 or a non-finite phi or u */
+  PFLB_ETIMEOUT = -5   /* a bounded device-side wait expired */
+} pflb_status;
+
+/* Phase-field model family (the four categories of Sec. II C and II D). */
+typedef enum pflb_family {
+  PFLB_CAC_FAKHARI2017 = 0, /* conservative Allen-Cahn, Sec. II C 1 */
+  PFLB_NLAC_CHAI2018 = 1,   /* nonlocal Allen-Cahn, Sec. II C 3 */
+  PFLB_HAC_HU2019 = 2,      /* hybrid Allen-Cahn with global weight lambda, Sec. II C 4 */
+  PFLB_CH_LIANG2014 = 3     /* Cahn-Hilliard with incompressible NS, Sec. II D 1 */
+} pflb_family;
+
+/* Population storage in device memory. Arithmetic is always FP32. The 16-bit
+ * forms store (value - w_a * c_a) / w_a with c_a = (phi_H + phi_L)/2 for g and
+ * 0 for f (w_a = 1 where a weight is zero): the deviation from the rest state
+ * scaled by the lattice weight. */
+typedef enum pflb_storage {
+  PFLB_FP32 = 0,
+  PFLB_FP16_DEV = 1,
+  PFLB_BF16_DEV = 2
+} pflb_storage;
+
+/* Nondimensional parameters of one run (lattice units). */
+typedef struct pflb_params {
+  int32_t dim;          /* 2 or 3 */
+  int32_t nx, ny, nz;   /* cells per axis; nz must be 1 in 2D */
+  int32_t family;       /* pflb_family */
+  int32_t storage;      /* pflb_storage */
+  int32_t bc_y;         /* 0 periodic; 1 resting walls; 2 walls moving in x
+                           (2D only): halfway bounce-back at y = -1/2 and
+                           y = ny - 1/2, mirrored phi ghosts */
+  int32_t visc_interp;  /* 0 linear kinematic viscosity (Eq. fakhari_mu_update);
+                           1 linear dynamic (Eq. mu_linear); 2 inverse-linear
+                           (Eq. mu_inverse); 3 logarithmic (Eq. mu_log) */
+  int32_t freeze_phi;   /* 1: the phase field is held fixed (Sec. III D) */
+  int32_t obs_capacity; /* length of the per-step observables ring, >= 1 */
+  double phi_H, phi_L;  /* bulk order parameters (Sec. II: 1 and 0) */
+  double rho_H, rho_L;  /* bulk densities */
+  double nu_H, nu_L;    /* bulk kinematic viscosities; tau = nu/c_s^2 + 1/2 */
+  double sigma;         /* surface tension */
+  double W;             /* interface thickness xi */
+  double M;             /* mobility M_phi; tau_phi = M/c_s^2 + 1/2
+                           (M/(eta c_s^2) + 1/2 for Cahn-Hilliard) */
+  double lambda_hybrid; /* Hu2019 weight lambda (Sec. III: 0.9) */
+  double eta_ch;        /* Liang2014 eta (paper leaves it free; 1) */
+  double gravity[3];    /* body force F_b = rho * gravity */
+  double force_density[3]; /* uniform force density added to F_b */
+  double lundgren_A;    /* linear forcing F = A rho u (turbulence driver) */
+  double wall_u[2];     /* x velocity of the bottom and top wall (bc_y = 2) */
+  double grad_eps;      /* |grad phi| below which the interface normal is 0 */
+} pflb_params;
+
+/* Bookkeeping of one state: sums over all cells of its macroscopic fields. */
+typedef struct pflb_obs {
+  int64_t step;         /* time level the fields belong to */
+  double sum_phi;       /* sum of phi (FP64 accumulation of FP32 terms) */
+  double vol_smooth;    /* sum (phi - phi_L)/(phi_H - phi_L), Eq. volume_continuous */
+  int64_t vol_count;    /* number of cells with phi > (phi_H + phi_L)/2 (Sec. IV A) */
+  double ke;            /* sum 1/2 rho |u|^2 */
+  double phi_max, phi_min;
+  double centroid[3];   /* sum x c / sum c with c = (phi - phi_L)/(phi_H - phi_L) */
+  int32_t status;       /* PFLB_OK or PFLB_EUNSTABLE */
+  int32_t pad;
+} pflb_obs;
+
+typedef struct pflb_handle pflb_handle;
+
+/* Validate the parameters, allocate the populations on the current device
+ * and bind the handle to `cuda_stream` (a cudaStream_t, may be NULL).
+ * PFLB_EINVAL for: dim not 2/3, sizes < 1, nz != 1 in 2D, walls in 3D or with ny < 4,
+ * phi_H == phi_L, W <= 0, sigma < 0, tau <= 1/2 for either phase, tau_phi <=
+ * 1/2, unknown family/storage/interpolation, obs_capacity < 1. */
+int pflb_create(const pflb_params* params, void* cuda_stream, pflb_handle** out);
+
+/* Set the state to equilibrium with the given phi and u and pressure 0
+ * (step count 0). phi0: N floats; u0: d*N floats or NULL for rest; host or
+ * device. For Cahn-Hilliard the chemical potential of phi0 enters g_eq
+ * (Eq. liang2_geq), computed with the Sec. III stencils. */
+int pflb_init(pflb_handle* h, const float* phi0, const float* u0);
+
+/* Advance nsteps >= 0 time steps, asynchronously on the handle's stream.
+ * One step: the macroscopic stage (phi, rho, nu, the stencils of Sec. III,
+ * chemical potential, forces, u, p), BGK collision of g and f with the
+ * family's equilibria and sources, streaming (g: two-array push; f: AA-pattern
+ * in place), and the observables of the pre-collision state into the
+ * per-step ring. Nonlocal and hybrid families first reduce the two integrals
+ * of Eq. (lagrange_multiplier) over the whole domain. Returns the sticky
+ * status known so far (instability is reported once the stream is
+ * synchronised). */
+int pflb_step(pflb_handle* h, int64_t nsteps);
+
+/* Wait for the handle's stream; returns PFLB_EUNSTABLE if any step flagged
+ * an instability. */
+int pflb_sync(pflb_handle* h);
+
+/* Observables of the current state (time level pflb_step_count). Runs one
+ * read-only pass, synchronises. */
+int pflb_observables(pflb_handle* h, pflb_obs* out);
+
+/* Copy the observables the last min(n, steps taken, obs_capacity) steps
+ * recorded (each the pre-collision state of its step), oldest first.
+ * *written receives the count. out: n pflb_obs in host memory. */
+int pflb_obs_history(pflb_handle* h, pflb_obs* out, int32_t n, int32_t* written);
+
+/* Macroscopic fields of the current state, as the next step's collision
+ * would compute them: phi (N), u (d*N, the force-corrected velocity), p (N,
+ * the thermodynamic pressure). Any pointer may be NULL. Host or device. */
+int pflb_get_fields(pflb_handle* h, float* phi, float* u, float* p);
+
+/* Size in floats of the canonical state: Qg*N populations g, Qf*N
+ * populations f (both post-streaming, i.e. what the next step reads, in the
+ * velocity order of pflb_lattice), then for Cahn-Hilliard d*N values of
+ * phi*u of the previous step. */
+int64_t pflb_state_floats(const pflb_handle* h);
+
+/* Write / read the canonical FP32 state (host or device buffer of
+ * pflb_state_floats floats). pflb_load keeps the step count. For FP16/BF16
+ * storage the values are decoded / encoded. */
+int pflb_save(pflb_handle* h, float* state);
+int pflb_load(pflb_handle* h, const float* state);
+
+/* Time levels advanced since pflb_init. */
+int64_t pflb_step_count(const pflb_handle* h);
+
+/* Algorithmic device-memory bytes per lattice update of one step (each
+ * stored population read once and written once, plus the phi*u field for
+ * Cahn-Hilliard and the extra read of g for the nonlocal reduction). */
+double pflb_bytes_per_update(const pflb_handle* h);
+
+/* Launch shape of the fused step: cells per block along the marching axis
+ * (z in 3D, y in 2D), 0 = library default. */
+int pflb_set_chunk(pflb_handle* h, int32_t chunk);
+
+/* Velocity set of a lattice in canonical order. which: 0 = phase field (g),
+ * 1 = hydrodynamics (f). q receives Q; e receives 3*Q ints (ex, ey, ez per
+ * velocity, ez = 0 in 2D) and w receives Q weights; either may be NULL. */
+int pflb_lattice(int32_t dim, int32_t which, int32_t* q, int32_t* e, double* w);
+
+int pflb_destroy(pflb_handle* h);
+const char* pflb_last_error(const pflb_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFLB_H */

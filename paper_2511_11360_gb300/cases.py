@@ -299,3 +299,79 @@ def batched_shear_sweep(count=512, sizes=(64, 128, 256, 512), seed=DEFAULT_SEED)
         W = int(rng.choice([3, 4, 5]))
         out.append(dict(L=L, family=fam, Ca=Ca, M=M, W=W))
     return out
+
+
+# --------------------------------------------------------------------------
+# Large 3D inputs generated on a torch device (same recipes as above)
+# --------------------------------------------------------------------------
+def solenoidal_field_torch(n, k0=4.0, u_rms=0.04, nmodes=48, seed=DEFAULT_SEED, kmax=8,
+                           device="cuda", dtype=None):
+    """solenoidal_field() on an n^3 periodic cube, evaluated with torch on
+    ``device``: the modes, directions and phases come from the same seeded
+    numpy draws; cos(k.x + theta) is built from separable complex
+    exponentials. Returns a (3, n, n, n) tensor."""
+    import torch
+    dtype = dtype or torch.float32
+    rng = np.random.default_rng(seed)
+    modes = []
+    while len(modes) < nmodes:
+        k = rng.integers(-kmax, kmax + 1, size=3)
+        if math.sqrt(float(np.sum(k * k))) < 1.0:
+            continue
+        modes.append(k)
+    ax = torch.arange(n, device=device, dtype=torch.float64)
+    u = torch.zeros((3, n, n, n), device=device, dtype=torch.float32)
+    for k in modes:
+        kvec = np.array([2 * math.pi * k[i] / n for i in range(3)])
+        kk = np.linalg.norm(kvec)
+        r = rng.normal(size=3)
+        q = r - np.dot(r, kvec) / kk ** 2 * kvec
+        q /= np.linalg.norm(q)
+        kmag = math.sqrt(float(np.sum(np.asarray(k, dtype=float) ** 2)))
+        amp = math.sqrt(kmag ** 4 * math.exp(-2 * kmag ** 2 / k0 ** 2)) / kmag
+        theta = rng.uniform(0, 2 * math.pi)
+        ex = torch.exp(1j * (kvec[0] * ax + theta))          # x
+        ey = torch.exp(1j * (kvec[1] * ax))                  # y
+        ez = torch.exp(1j * (kvec[2] * ax))                  # z
+        c = (ez[:, None, None] * ey[None, :, None] * ex[None, None, :]).real.to(torch.float32)
+        for i in range(3):
+            u[i].add_(c, alpha=float(amp * q[i]))
+        del c
+    rms = torch.sqrt(torch.mean(torch.sum(u.double() ** 2, dim=0)) / 3.0).item()
+    u.mul_(u_rms / rms)
+    return u.to(dtype)
+
+
+def droplet_field_torch(n, centres, R, W, device="cuda"):
+    """droplet_field() on a torch device (float32)."""
+    import torch
+    phi = torch.zeros((n, n, n), device=device, dtype=torch.float32)
+    h = int(math.ceil(R + 5 * W))
+    off = torch.arange(-h, h + 1, device=device)
+    for c in centres:
+        ic = [int(math.floor(v)) for v in c]
+        ix = (ic[0] + off) % n
+        iy = (ic[1] + off) % n
+        iz = (ic[2] + off) % n
+        dx = (ic[0] + off + 0.5).double() - c[0]
+        dy = (ic[1] + off + 0.5).double() - c[1]
+        dz = (ic[2] + off + 0.5).double() - c[2]
+        r = torch.sqrt(dz[:, None, None] ** 2 + dy[None, :, None] ** 2 + dx[None, None, :] ** 2)
+        blob = (0.5 + 0.5 * torch.tanh(2.0 * (R - r) / W)).to(torch.float32)
+        sub = phi[iz[:, None, None], iy[None, :, None], ix[None, None, :]]
+        phi[iz[:, None, None], iy[None, :, None], ix[None, None, :]] = torch.maximum(sub, blob)
+    return phi
+
+
+def hit_droplets_3d_torch(n=512, count=200, R=16.0, W=4.0, We=5.0, u_rms=0.04, nu=0.006,
+                          M=0.01, lundgren_A=1e-4, seed=DEFAULT_SEED, family=FAKHARI2017,
+                          device="cuda", **kw):
+    """hit_droplets_3d() with the fields generated on a torch device."""
+    centres = place_droplets(n, count, R, W, seed=seed)
+    phi = droplet_field_torch(n, centres, R, W, device=device)
+    u = solenoidal_field_torch(n, u_rms=u_rms, seed=seed + 1, device=device)
+    sigma = 1.0 * u_rms ** 2 * (2 * R) / We
+    P = params(dim=3, nx=n, ny=n, nz=n, family=family, rho_H=1.0, rho_L=1.0,
+               nu_H=nu, nu_L=nu, sigma=sigma, W=W, M=M, lundgren_A=lundgren_A)
+    P.update(kw)
+    return P, phi, u, centres

@@ -1,0 +1,70 @@
+// Launch arguments of the PF-LB kernels and the host-side entry points of
+// each translation unit (no kernel code here).
+#pragma once
+
+#include "pflb_common.cuh"
+
+namespace pflb {
+
+struct StepArgs {
+  DevParams p;
+  const void* g_src;
+  void* g_dst;
+  void* f;
+  float* phiu;            // Cahn-Hilliard: phi*u of the previous step (d x N), in place
+  DevObs* obs_slot;       // accumulate the observables here
+  DevObs* obs_zero;       // zero this slot (the next step's), may be null
+  const double* gamma_acc;// nonlocal/hybrid: (I1, I2) of this step
+  int parity;             // 0: even step, 1: odd step (AA pattern)
+  int macro;              // 1: write fields, no populations
+  float* out_phi;
+  float* out_u;
+  float* out_p;
+  int chunk;              // cells per block along the marching axis
+  long long N;
+};
+
+struct InitArgs {
+  DevParams p;
+  const float* phi0;
+  const float* u0;        // may be null (rest)
+  void* g;
+  void* f;
+  float* phiu;
+  long long N;
+};
+
+struct GammaArgs {
+  DevParams p;
+  const void* g_src;
+  double* acc;            // (I1, I2) accumulated here
+  double* zero;           // zeroed (the next step's pair), may be null
+  long long N;
+};
+
+struct CanonArgs {
+  DevParams p;
+  void* g;                // current source g
+  void* f;                // AA buffer
+  float* phiu;
+  float* state;           // canonical FP32 state
+  int parity;             // parity of the next step
+  int to_canon;           // 1: storage -> state (save); 0: state -> storage (load)
+  int ch;                 // Cahn-Hilliard (phi*u block present, g_0 stored in 3D)
+  long long N;
+};
+
+// Per-family translation units.
+void step_fakhari(int dim, int storage, const StepArgs& a, cudaStream_t s);
+void step_chai(int dim, int storage, const StepArgs& a, cudaStream_t s);
+void step_hu(int dim, int storage, const StepArgs& a, cudaStream_t s);
+void step_liang2014(int dim, int storage, const StepArgs& a, cudaStream_t s);
+void init_fakhari(int dim, int storage, const InitArgs& a, cudaStream_t s);
+void init_chai(int dim, int storage, const InitArgs& a, cudaStream_t s);
+void init_hu(int dim, int storage, const InitArgs& a, cudaStream_t s);
+void init_liang2014(int dim, int storage, const InitArgs& a, cudaStream_t s);
+// pflb_aux.cu
+void gamma_sums(int dim, int storage, const GammaArgs& a, cudaStream_t s);
+void canon_copy(int dim, int storage, const CanonArgs& a, cudaStream_t s);
+
+}  // namespace pflb

@@ -1,0 +1,655 @@
+// The fused coupled PF-LB step kernel (one launch per time step).
+//
+// Each block owns a tile of TA x TB cells across the fast axes and marches a
+// chunk of cells along the slow axis (z in 3D, y in 2D). The order parameter
+// of the planes around the current one lives in a shared-memory ring (radius
+// 1 for the Allen-Cahn families, 2 for Cahn-Hilliard, whose chemical
+// potential needs its own Laplacian and lives in a second ring). Each new
+// plane's phi is recomputed from the incoming g populations of the tile and
+// its halo, so phi is never written to device memory.
+//
+// Streaming: g uses two arrays (read one, push into the other), which keeps
+// the g read by a neighbouring block's halo unmodified during the step; f
+// uses the AA pattern in place (even steps read and write the cell's own
+// slots, reversed; odd steps read from and write to the neighbours).
+// Halfway bounce-back walls (2D, y ends) reflect into the cell's own slots.
+#pragma once
+
+#include "pflb_args.h"
+
+namespace pflb {
+
+template <int DIM> struct Geom;
+template <> struct Geom<3> { static constexpr int TA = 32, TB = 8, MINB = 2; };
+template <> struct Geom<2> { static constexpr int TA = 128, TB = 1, MINB = 4; };
+
+
+
+// Kernel-space offsets of a physical lattice velocity: (a, b, c) = (x, y, z)
+// in 3D and (x, -, y) in 2D.
+template <int DIM, typename L>
+__device__ __forceinline__ constexpr int da_of(int q) { return L::ex(q); }
+template <int DIM, typename L>
+__device__ __forceinline__ constexpr int db_of(int q) { return DIM == 3 ? L::ey(q) : 0; }
+template <int DIM, typename L>
+__device__ __forceinline__ constexpr int dc_of(int q) { return DIM == 3 ? L::ez(q) : L::ey(q); }
+
+// Physical component k of a velocity.
+template <typename L>
+__device__ __forceinline__ constexpr int ecomp(int q, int k) {
+  return k == 0 ? L::ex(q) : (k == 1 ? L::ey(q) : L::ez(q));
+}
+
+__device__ __forceinline__ int wrap_mod(int v, int n) {
+  int m = v % n;
+  return m < 0 ? m + n : m;
+}
+
+// Kinematic viscosity, Eqs. (fakhari_mu_update), (mu_linear), (mu_inverse), (mu_log).
+__device__ __forceinline__ float viscosity(const DevParams& P, float phi, float rho) {
+  const float t = (phi - P.phiL) * P.inv_dphi;
+  switch (P.visc_interp) {
+    case 0: return P.nuL + (P.nuH - P.nuL) * t;
+    case 1: return (P.muL + (P.muH - P.muL) * t) / rho;
+    case 2: return P.muH * P.muL / (t * P.muL + (1.0f - t) * P.muH) / rho;
+    default: return expf(t * logf(P.muH) + (1.0f - t) * logf(P.muL)) / rho;
+  }
+}
+
+// phi from phi* = sum g: identity for Fakhari2017/Liang2014; for
+// Chai2018/Hu2019 phi = phi* + (1 - lambda) R(phi*)/2 (Eq. chai2018_phi_update,
+// evaluated at phi*).
+template <int FAM>
+__device__ __forceinline__ float nonlocal_R(const DevParams& P, float ps, float gamma) {
+  return P.M * (-P.four_beta_over_kappa * (ps - P.phiH) * (ps - P.phiL) * (ps - P.phi0) +
+                gamma * (P.phiH - ps) * (ps - P.phiL));
+}
+template <int FAM>
+__device__ __forceinline__ float finish_phi(const DevParams& P, float ps, float gamma) {
+  if constexpr (FAM == FAM_CHAI) return ps + 0.5f * nonlocal_R<FAM>(P, ps, gamma);
+  else if constexpr (FAM == FAM_HU) return ps + 0.5f * (1.0f - P.lambda) * nonlocal_R<FAM>(P, ps, gamma);
+  else return ps;
+}
+
+// ---------------------------------------------------------------------------
+// Collision of one cell. Inputs: pre-collision g, f; phi, phi*, grad phi,
+// lap phi (and for Cahn-Hilliard mu, lap mu, phi*u of the previous step).
+// Outputs: post-collision g*, f*, u, p, rho.
+// ---------------------------------------------------------------------------
+template <int FAM, int DIM>
+struct Cell {
+  using LG = typename Lattices<DIM>::G;
+  using LF = typename Lattices<DIM>::F;
+  static constexpr int QG = LG::Q, QF = LF::Q;
+
+  __device__ __forceinline__ static void collide(
+      const DevParams& P, float (&g)[QG], float (&f)[QF], float phi, float phis,
+      const float (&gp)[DIM], float lp, float mu_in, float lmu, float (&phiu)[DIM],
+      float gamma, float (&u)[DIM], float& rho, float& p) {
+    constexpr float cs2 = 1.0f / 3.0f;
+    rho = P.rhoL + P.drho_dphi * (phi - P.phiL);
+    const float nu = viscosity(P, phi, rho);
+    const float itau = 1.0f / (3.0f * nu + 0.5f);
+    const float fw = 1.0f - 0.5f * itau;
+    const float inv_rho = 1.0f / rho;
+    float grho[DIM], Fs[DIM], Fb[DIM], mom[DIM];
+    float sumf = 0.0f;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) mom[k] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < QF; ++q) {
+      sumf += f[q];
+#pragma unroll
+      for (int k = 0; k < DIM; ++k)
+        if (ecomp<LF>(q, k) != 0) mom[k] += (float)ecomp<LF>(q, k) * f[q];
+    }
+    const float mu = (FAM == FAM_LIANG) ? mu_in
+        : P.beta4 * (phi - P.phiH) * (phi - P.phiL) * (phi - P.phi0) - P.kappa * lp;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      grho[k] = P.drho_dphi * gp[k];
+      Fs[k] = mu * gp[k];
+      Fb[k] = rho * P.grav[k] + P.fdens[k];
+    }
+    const float A = P.lundA;
+    float F[DIM];
+
+    if constexpr (FAM != FAM_LIANG) {
+      // Pressure p = rho c_s^2 sum f (Eq. fakhari_p_update); F_p = -(p/rho) grad rho.
+      p = rho * cs2 * sumf;
+      float Fo[DIM];
+      const float inv_1mA = 1.0f / (1.0f - 0.5f * A);
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) Fo[k] = Fs[k] + Fb[k] - cs2 * sumf * grho[k];
+      if (P.drho_dphi != 0.0f) {
+        // F_mu = nu [grad u + grad u^T] . grad rho with the strain rate from the
+        // local non-equilibrium second moment (Reading R3):
+        // S_ij = -3 (Pi_ij - sum f/3 d_ij - u'_i u'_j) / tau.
+        float u1[DIM];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) u1[k] = (mom[k] + 0.5f * inv_rho * Fo[k]) * inv_1mA;
+        float Pi[DIM][DIM];
+#pragma unroll
+        for (int i = 0; i < DIM; ++i)
+#pragma unroll
+          for (int j = 0; j < DIM; ++j) Pi[i][j] = 0.0f;
+#pragma unroll
+        for (int q = 0; q < QF; ++q)
+#pragma unroll
+          for (int i = 0; i < DIM; ++i)
+#pragma unroll
+            for (int j = i; j < DIM; ++j)
+              if (ecomp<LF>(q, i) * ecomp<LF>(q, j) != 0)
+                Pi[i][j] += (float)(ecomp<LF>(q, i) * ecomp<LF>(q, j)) * f[q];
+        const float c = -3.0f * nu * itau;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+          float s = 0.0f;
+#pragma unroll
+          for (int j = 0; j < DIM; ++j) {
+            const float pij = (i <= j ? Pi[i][j] : Pi[j][i]) - (i == j ? cs2 * sumf : 0.0f) - u1[i] * u1[j];
+            s += pij * grho[j];
+          }
+          Fo[i] += c * s;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        u[k] = (mom[k] + 0.5f * inv_rho * Fo[k]) * inv_1mA;  // Eq. (fakhari_velocity_update)
+        F[k] = Fo[k] + A * rho * u[k];
+      }
+    } else {
+      // Liang2014: u from Eq. (liang2014_velocity_update); F_a = drho/dphi div(M grad mu) u.
+      const float acoef = P.drho_dphi * P.M * lmu;
+      const float den = 1.0f / (rho - 0.5f * acoef - 0.5f * A * rho);
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        u[k] = (mom[k] + 0.5f * (Fs[k] + Fb[k])) * den;
+        F[k] = Fs[k] + Fb[k] + (acoef + A * rho) * u[k];
+      }
+    }
+    float usq = 0.0f;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) usq += u[k] * u[k];
+
+    // ---------------- phase field ----------------
+    if constexpr (FAM == FAM_LIANG) {
+      // Eq. (liang2_geq) and Eq. (liang2_G) with the backward-Euler d_t(phi u).
+      const float emu = P.eta * mu;
+      float pu[DIM], dpu[DIM];
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        pu[k] = phi * u[k];
+        dpu[k] = pu[k] - phiu[k];
+        phiu[k] = pu[k];
+      }
+#pragma unroll
+      for (int q = 0; q < QG; ++q) {
+        float epu = 0.0f, edpu = 0.0f;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+          if (ecomp<LG>(q, k) != 0) {
+            epu += (float)ecomp<LG>(q, k) * pu[k];
+            edpu += (float)ecomp<LG>(q, k) * dpu[k];
+          }
+        const float w = LG::w(q);
+        const float geq = (q == 0) ? phi + (w - 1.0f) * emu : w * (emu + 3.0f * epu);
+        const float G = 3.0f * w * edpu;
+        g[q] = g[q] - (g[q] - geq) * P.inv_tau_phi + P.src_w_phi * G;
+      }
+    } else {
+      float flux[DIM];
+      bool has_cons = (FAM == FAM_FAKHARI || FAM == FAM_HU);
+      if (has_cons) {
+        // Conservative counter term, Eq. (fakhari_G_modified); Reading R6 guard.
+        float g2 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) g2 += gp[k] * gp[k];
+        const float s = (g2 >= P.eps2) ? P.counter_k * (P.phiH - phi) * (phi - P.phiL) * rsqrtf(g2) : 0.0f;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) flux[k] = s * gp[k];
+      }
+      float Rw = 0.0f, lam = 1.0f;
+      if constexpr (FAM == FAM_CHAI || FAM == FAM_HU) {
+        Rw = nonlocal_R<FAM>(P, phis, gamma);
+        if constexpr (FAM == FAM_HU) { lam = P.lambda; Rw *= (1.0f - lam); }
+      }
+#pragma unroll
+      for (int q = 0; q < QG; ++q) {
+        float eu = 0.0f, ef = 0.0f;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+          if (ecomp<LG>(q, k) != 0) {
+            eu += (float)ecomp<LG>(q, k) * u[k];
+            if (has_cons) ef += (float)ecomp<LG>(q, k) * flux[k];
+          }
+        const float w = LG::w(q);
+        float geq;
+        if constexpr (FAM == FAM_FAKHARI)
+          geq = w * phi * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * usq);  // Eq. (fakhari_geq)
+        else
+          geq = w * phi * (1.0f + 3.0f * eu);                               // Eq. (Chai_geq)
+        float G;
+        if constexpr (FAM == FAM_FAKHARI) G = w * ef;
+        else if constexpr (FAM == FAM_CHAI) G = w * Rw;
+        else G = w * (lam * ef + Rw);                                       // Eq. (Hu_G)
+        g[q] = g[q] - (g[q] - geq) * P.inv_tau_phi + P.src_w_phi * G;
+      }
+    }
+
+    // ---------------- hydrodynamics ----------------
+    if constexpr (FAM == FAM_LIANG) {
+      // p by Eq. (liang_p_update); pressure-based f_eq and forcing of Eqs.
+      // (liang2_feq), (liang2_F), (Gamma_beta).
+      const float w0 = LF::w(0);
+      float udg = 0.0f;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) udg += u[k] * grho[k];
+      p = cs2 / (1.0f - w0) * (sumf - f[0] + 0.5f * udg - rho * w0 * 1.5f * usq);
+      float uF = 0.0f, ua = 0.0f;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        uF += u[k] * F[k];
+        ua += u[k] * cs2 * grho[k];
+      }
+#pragma unroll
+      for (int q = 0; q < QF; ++q) {
+        float eu = 0.0f, eF = 0.0f, ea = 0.0f;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+          if (ecomp<LF>(q, k) != 0) {
+            const float e = (float)ecomp<LF>(q, k);
+            eu += e * u[k];
+            eF += e * F[k];
+            ea += e * cs2 * grho[k];
+          }
+        const float w = LF::w(q);
+        const float Gam = w * (3.0f * eu + 4.5f * eu * eu - 1.5f * usq);
+        const float feq = (q == 0) ? 3.0f * p * (w - 1.0f) + rho * w * (-1.5f * usq)
+                                   : 3.0f * p * w + rho * Gam;
+        const float Fq = 3.0f * ((ea - ua) * Gam + (eF - uF) * (w + Gam));
+        f[q] = f[q] - (f[q] - feq) * itau + fw * Fq;
+      }
+    } else {
+      float Ft[DIM], uFt = 0.0f;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        Ft[k] = F[k] * inv_rho;
+        uFt += u[k] * Ft[k];
+      }
+#pragma unroll
+      for (int q = 0; q < QF; ++q) {
+        float eu = 0.0f, eF = 0.0f;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+          if (ecomp<LF>(q, k) != 0) {
+            const float e = (float)ecomp<LF>(q, k);
+            eu += e * u[k];
+            eF += e * Ft[k];
+          }
+        const float w = LF::w(q);
+        const float feq = w * (sumf + 3.0f * eu + 4.5f * eu * eu - 1.5f * usq);  // Eq. (fakhari_feq)
+        float Fq;
+        if constexpr (FAM == FAM_FAKHARI) Fq = 3.0f * w * eF;                     // Eq. (fakhari_F)
+        else Fq = w * (3.0f * eF + 9.0f * (eu * eF - cs2 * uFt));                 // Eq. (chai_F), Reading R2
+        f[q] = f[q] - (f[q] - feq) * itau + fw * Fq;
+      }
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// The kernel.
+// ---------------------------------------------------------------------------
+template <int FAM, int DIM, typename T>
+__global__ void __launch_bounds__(Geom<DIM>::TA * Geom<DIM>::TB, Geom<DIM>::MINB)
+step_kernel(const StepArgs args) {
+  using LG = typename Lattices<DIM>::G;
+  using LF = typename Lattices<DIM>::F;
+  using LS = typename Lattices<DIM>::S;
+  constexpr int QG = LG::Q, QF = LF::Q, QS = LS::Q;
+  constexpr int TA = Geom<DIM>::TA, TB = Geom<DIM>::TB, NT = TA * TB;
+  constexpr bool CH = (FAM == FAM_LIANG);
+  constexpr int H = CH ? 2 : 1;                 // phi halo
+  constexpr int HB = (DIM == 3) ? H : 0;
+  constexpr int RA = TA + 2 * H, RB = TB + 2 * HB, PLANE = RA * RB;
+  constexpr int NSLOT = 2 * H + 2;
+  constexpr int NHALO = PLANE - NT;
+  constexpr int KH = (NHALO + NT - 1) / NT;
+  constexpr int MHB = (DIM == 3) ? 1 : 0;       // mu region halo (CH)
+  constexpr int MRA = TA + 2, MRB = TB + 2 * MHB, MPLANE = MRA * MRB;
+  constexpr int MSLOT = 4;
+  constexpr int MHALO = MPLANE - NT;
+  constexpr int KM = (MHALO + NT - 1) / NT;
+
+  __shared__ float s_phi[NSLOT * PLANE];
+  __shared__ float s_mu[CH ? MSLOT * MPLANE : 1];
+  __shared__ double s_red[(NT / 32) * 10];
+
+  const DevParams& P = args.p;
+  const int NA = P.nx, NB = (DIM == 3) ? P.ny : 1, NC = (DIM == 3) ? P.nz : P.ny;
+  const long long N = args.N;
+  const long long NAB = (long long)NA * NB;
+  const int tiles_a = (NA + TA - 1) / TA, tiles_b = (NB + TB - 1) / TB;
+  int bid = blockIdx.x;
+  const int ti = bid % tiles_a;
+  bid /= tiles_a;
+  const int tj = bid % tiles_b;
+  bid /= tiles_b;
+  const int a0 = ti * TA, b0 = tj * TB;
+  const int c0 = bid * args.chunk;
+  const int c1 = min(c0 + args.chunk, NC);
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = tx + TA * ty;
+  const int a = a0 + tx, b = b0 + ty;
+  const bool active = (a < NA) && (b < NB);
+  const bool walls = P.walls != 0;
+
+  if (args.obs_zero != nullptr && blockIdx.x == 0 && tid == 0) obs_zero_slot(args.obs_zero);
+
+  float gamma = 0.0f;
+  if constexpr (FAM == FAM_CHAI || FAM == FAM_HU) {
+    const double I2 = args.gamma_acc[1];
+    gamma = (I2 != 0.0) ? (float)(args.gamma_acc[0] / I2) : 0.0f;
+  }
+
+  const T* gsrc = static_cast<const T*>(args.g_src);
+  T* gdst = static_cast<T*>(args.g_dst);
+  T* fb = static_cast<T*>(args.f);
+
+  // Ring cells of this thread: its own cell and KH halo cells (constant
+  // across the march). Offsets are wrapped (a, b) linear offsets.
+  const int own_ab = wrap_mod(a, NA) + NA * wrap_mod(b, NB);
+  const int own_slot = (ty + HB) * RA + (tx + H);
+  int halo_ab[KH], halo_pos[KH];
+#pragma unroll
+  for (int k = 0; k < KH; ++k) {
+    int hk = tid + k * NT;
+    halo_pos[k] = -1;
+    halo_ab[k] = 0;
+    if (hk < NHALO) {
+      int ra, rb;
+      if (hk < HB * RA) { rb = hk / RA; ra = hk % RA; }
+      else {
+        hk -= HB * RA;
+        if (hk < HB * RA) { rb = HB + TB + hk / RA; ra = hk % RA; }
+        else {
+          hk -= HB * RA;
+          rb = HB + hk / (2 * H);
+          const int j = hk % (2 * H);
+          ra = (j < H) ? j : TA + j;
+        }
+      }
+      halo_pos[k] = rb * RA + ra;
+      halo_ab[k] = wrap_mod(a0 - H + ra, NA) + NA * wrap_mod(b0 - HB + rb, NB);
+    }
+  }
+
+  // Plane index along the marching axis: periodic wrap, or mirror at walls.
+  auto map_c = [&](int c) -> int {
+    if (walls) {
+      if (c < 0) return -1 - c;
+      if (c >= NC) return 2 * NC - 1 - c;
+      return c;
+    }
+    return wrap_mod(c, NC);
+  };
+
+  auto load_g = [&](long long idx, float (&gv)[QG]) -> float {
+    float s = 0.0f;
+#pragma unroll
+    for (int q = 0; q < QG; ++q) {
+      if (DIM == 3 && !CH && q == 0) { gv[q] = 0.0f; continue; }  // D3Q7 rest slot: w_0 = 0, g_0 = 0
+      gv[q] = Codec<T>::load(gsrc + (long long)q * N + idx, norm_w<LG>(q), P.gref);
+      s += gv[q];
+    }
+    return s;
+  };
+
+  // Compute phi of logical plane c into ring slot; keep the own cell's g.
+  auto produce = [&](int c, float (&gown)[QG]) {
+    const long long pofs = NAB * map_c(c);
+    float* slot = s_phi + ((c % NSLOT + NSLOT) % NSLOT) * PLANE;
+    const float ps = load_g(own_ab + pofs, gown);
+    slot[own_slot] = finish_phi<FAM>(P, ps, gamma);
+#pragma unroll
+    for (int k = 0; k < KH; ++k) {
+      if (halo_pos[k] >= 0) {
+        float tmp[QG];
+        const float hs = load_g(halo_ab[k] + pofs, tmp);
+        slot[halo_pos[k]] = finish_phi<FAM>(P, hs, gamma);
+      }
+    }
+  };
+
+  auto phi_at = [&](int c, int ra, int rb) -> float {
+    return s_phi[((c % NSLOT + NSLOT) % NSLOT) * PLANE + rb * RA + ra];
+  };
+
+  // Cahn-Hilliard: mu of logical plane c over the tile + 1 region.
+  auto make_mu = [&](int c) {
+    float* mslot = s_mu + ((c % MSLOT + MSLOT) % MSLOT) * MPLANE;
+    auto one = [&](int ma, int mb) {
+      const int ra = ma + H - 1, rb = mb + HB - MHB;
+      const float pc = phi_at(c, ra, rb);
+      float lap = 0.0f;
+#pragma unroll
+      for (int q = 1; q < QS; ++q)
+        lap += LS::w(q) * (phi_at(c + dc_of<DIM, LS>(q), ra + da_of<DIM, LS>(q), rb + db_of<DIM, LS>(q)) - pc);
+      lap *= 6.0f;
+      mslot[mb * MRA + ma] = P.beta4 * (pc - P.phiH) * (pc - P.phiL) * (pc - P.phi0) - P.kappa * lap;
+    };
+    one(tx + 1, ty + MHB);
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+      int hk = tid + k * NT;
+      if (hk < MHALO) {
+        int ma, mb;
+        if (hk < MHB * MRA) { mb = hk / MRA; ma = hk % MRA; }
+        else {
+          hk -= MHB * MRA;
+          if (hk < MHB * MRA) { mb = MHB + TB + hk / MRA; ma = hk % MRA; }
+          else {
+            hk -= MHB * MRA;
+            mb = MHB + hk / 2;
+            ma = (hk % 2 == 0) ? 0 : TA + 1;
+          }
+        }
+        one(ma, mb);
+      }
+    }
+  };
+
+  ObsPartial obs;
+  obs_init(obs);
+
+  float g0[QG], g1[QG], g2[QG];
+  // Prologue: planes c0-H .. c0+H-1.
+  {
+    float tmp[QG];
+#pragma unroll
+    for (int h = H; h >= 1; --h) produce(c0 - h, tmp);
+    produce(c0, g0);
+    if constexpr (CH) produce(c0 + 1, g1);
+  }
+  if constexpr (CH) {
+    __syncthreads();
+    make_mu(c0 - 1);
+    make_mu(c0);
+  }
+
+  // Own-cell neighbour coordinates along the fast axes (constant).
+  const int aw = (a < NA) ? a : 0, bw = (b < NB) ? b : 0;
+  const int am = aw == 0 ? NA - 1 : aw - 1, ap = aw == NA - 1 ? 0 : aw + 1;
+  const int bm = bw == 0 ? NB - 1 : bw - 1, bp = bw == NB - 1 ? 0 : bw + 1;
+  auto A_of = [&](int d) { return d < 0 ? am : (d > 0 ? ap : aw); };
+  auto B_of = [&](int d) { return d < 0 ? bm : (d > 0 ? bp : bw); };
+
+  for (int c = c0; c < c1; ++c) {
+    if constexpr (CH) {
+      produce(c + 2, g2);
+      __syncthreads();
+      make_mu(c + 1);
+      __syncthreads();
+    } else {
+      produce(c + 1, g1);
+      __syncthreads();
+    }
+
+    if (active) {
+      // Stencils of Sec. III on the ring (stencil lattice weights).
+      const int ra = tx + H, rb = ty + HB;
+      const float pc = phi_at(c, ra, rb);
+      float gp[DIM], lp = 0.0f;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) gp[k] = 0.0f;
+#pragma unroll
+      for (int q = 1; q < QS; ++q) {
+        const float v = phi_at(c + dc_of<DIM, LS>(q), ra + da_of<DIM, LS>(q), rb + db_of<DIM, LS>(q));
+        lp += LS::w(q) * (v - pc);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+          if (ecomp<LS>(q, k) != 0) gp[k] += LS::w(q) * (float)ecomp<LS>(q, k) * v;
+      }
+      lp *= 6.0f;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) gp[k] *= 3.0f;
+
+      float mu_c = 0.0f, lmu = 0.0f;
+      if constexpr (CH) {
+        auto mu_at = [&](int cc, int ma, int mb) {
+          return s_mu[((cc % MSLOT + MSLOT) % MSLOT) * MPLANE + mb * MRA + ma];
+        };
+        const int ma = tx + 1, mb = ty + MHB;
+        mu_c = mu_at(c, ma, mb);
+#pragma unroll
+        for (int q = 1; q < QS; ++q)
+          lmu += LS::w(q) * (mu_at(c + dc_of<DIM, LS>(q), ma + da_of<DIM, LS>(q), mb + db_of<DIM, LS>(q)) - mu_c);
+        lmu *= 6.0f;
+      }
+
+      const int cm = (c == 0) ? NC - 1 : c - 1, cp = (c == NC - 1) ? 0 : c + 1;
+      const bool lo_wall = walls && c == 0, hi_wall = walls && c == NC - 1;
+      auto C_of = [&](int d) { return d < 0 ? cm : (d > 0 ? cp : c); };
+      auto crosses = [&](int dcv) { return (dcv < 0 && lo_wall) || (dcv > 0 && hi_wall); };
+      const long long idx = (long long)aw + NA * ((long long)bw + (long long)NB * c);
+      auto nidx = [&](int da, int db, int dc) -> long long {
+        return (long long)A_of(da) + NA * ((long long)B_of(db) + (long long)NB * C_of(dc));
+      };
+
+      // Pre-collision f (AA pattern).
+      float f[QF];
+#pragma unroll
+      for (int q = 0; q < QF; ++q) {
+        const int da = da_of<DIM, LF>(q), db = db_of<DIM, LF>(q), dc = dc_of<DIM, LF>(q);
+        const float wn = norm_w<LF>(q);
+        if (args.parity == 0) {
+          f[q] = Codec<T>::loadc(fb + (long long)q * N + idx, wn, 0.0f);
+        } else if (crosses(-dc)) {
+          f[q] = Codec<T>::loadc(fb + (long long)q * N + idx, wn, 0.0f);
+        } else {
+          f[q] = Codec<T>::loadc(fb + (long long)LF::opp(q) * N + nidx(-da, -db, -dc), norm_w<LF>(LF::opp(q)), 0.0f);
+        }
+      }
+      float phiu[DIM];
+      if constexpr (CH) {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) phiu[k] = args.phiu[(long long)k * N + idx];
+      }
+      float phis = 0.0f;
+#pragma unroll
+      for (int q = 0; q < QG; ++q) phis += g0[q];
+
+      float u[DIM], rho, p;
+      float gnew[QG];
+#pragma unroll
+      for (int q = 0; q < QG; ++q) gnew[q] = g0[q];
+      Cell<FAM, DIM>::collide(P, gnew, f, pc, phis, gp, lp, mu_c, lmu, phiu, gamma, u, rho, p);
+
+      // Observables of the pre-collision state.
+      {
+        comp_add(obs.s_hi, obs.s_lo, pc);
+        const float fr = (pc - P.phiL) * P.inv_dphi;
+        float usq = 0.0f;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) usq += u[k] * u[k];
+        obs.vs += fr;
+        obs.ke += 0.5f * rho * usq;
+        obs.cx += (float)aw * fr;
+        obs.cy += (float)(DIM == 3 ? bw : c) * fr;
+        obs.cz += (float)(DIM == 3 ? c : 0) * fr;
+        obs.count += (pc > P.phi0) ? 1u : 0u;
+        obs.mx = fmaxf(obs.mx, pc);
+        obs.mn = fminf(obs.mn, pc);
+        if (!(isfinite(pc) && isfinite(usq) && rho > 0.0f)) obs.bad = 1u;
+      }
+
+      if (args.macro) {
+        args.out_phi[idx] = pc;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) args.out_u[(long long)k * N + idx] = u[k];
+        args.out_p[idx] = p;
+      } else {
+        if constexpr (CH) {
+#pragma unroll
+          for (int k = 0; k < DIM; ++k) args.phiu[(long long)k * N + idx] = phiu[k];
+        }
+        // g: two-array push, bounce-back into the own cell at walls.
+        const float uw_lo = P.moving ? P.wall_u[0] : 0.0f, uw_hi = P.moving ? P.wall_u[1] : 0.0f;
+#pragma unroll
+        for (int q = 0; q < QG; ++q) {
+          if (DIM == 3 && !CH && q == 0) continue;
+          const int da = da_of<DIM, LG>(q), db = db_of<DIM, LG>(q), dc = dc_of<DIM, LG>(q);
+          const float wn = norm_w<LG>(q);
+          if (P.freeze) {
+            Codec<T>::store(gdst + (long long)q * N + idx, g0[q], wn, P.gref);
+          } else if (crosses(dc)) {
+            const float uw = dc < 0 ? uw_lo : uw_hi;
+            const float v = gnew[q] - 6.0f * LG::w(q) * pc * (float)LG::ex(q) * uw;
+            Codec<T>::store(gdst + (long long)LG::opp(q) * N + idx, v, norm_w<LG>(LG::opp(q)), P.gref);
+          } else {
+            Codec<T>::store(gdst + (long long)q * N + nidx(da, db, dc), gnew[q], wn, P.gref);
+          }
+        }
+        // f: AA pattern.
+        const float sc = CH ? rho : 1.0f;
+#pragma unroll
+        for (int q = 0; q < QF; ++q) {
+          const int da = da_of<DIM, LF>(q), db = db_of<DIM, LF>(q), dc = dc_of<DIM, LF>(q);
+          float v = f[q];
+          const bool cr = crosses(dc);
+          if (cr) {
+            const float uw = dc < 0 ? uw_lo : uw_hi;
+            v -= 6.0f * LF::w(q) * sc * (float)LF::ex(q) * uw;
+          }
+          if (args.parity == 0 || cr) {
+            Codec<T>::store(fb + (long long)LF::opp(q) * N + idx, v, norm_w<LF>(LF::opp(q)), 0.0f);
+          } else {
+            Codec<T>::store(fb + (long long)q * N + nidx(da, db, dc), v, norm_w<LF>(q), 0.0f);
+          }
+        }
+      }
+    }
+
+    // Rotate the own-cell g pipeline.
+#pragma unroll
+    for (int q = 0; q < QG; ++q) {
+      g0[q] = g1[q];
+      if constexpr (CH) g1[q] = g2[q];
+    }
+  }
+
+  obs_block_commit(obs, args.obs_slot, s_red);
+}
+
+template <int FAM, int DIM, typename T>
+void launch_step(const StepArgs& args, cudaStream_t stream) {
+  constexpr int TA = Geom<DIM>::TA, TB = Geom<DIM>::TB;
+  const int NA = args.p.nx, NB = (DIM == 3) ? args.p.ny : 1, NC = (DIM == 3) ? args.p.nz : args.p.ny;
+  const long long tiles = (long long)((NA + TA - 1) / TA) * ((NB + TB - 1) / TB);
+  const long long chunks = (NC + args.chunk - 1) / args.chunk;
+  dim3 block(TA, TB, 1);
+  step_kernel<FAM, DIM, T><<<(unsigned)(tiles * chunks), block, 0, stream>>>(args);
+}
+
+}  // namespace pflb

@@ -1,0 +1,261 @@
+"""ctypes binding of libpflb (the C ABI in include/pflb.h).
+
+Argument marshalling only: every step of the coupled PF-LB update runs in the
+CUDA library. Buffers may be numpy arrays (host) or objects exposing
+``data_ptr()`` (e.g. torch CUDA tensors); streams may be an integer handle or
+an object with ``cuda_stream``. There is no CPU implementation: if the
+library cannot be loaded, or no CUDA device exists, the calls raise.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libpflb.so")
+
+PFLB_OK, PFLB_EINVAL, PFLB_ENOMEM, PFLB_ECUDA, PFLB_EUNSTABLE, PFLB_ETIMEOUT = 0, -1, -2, -3, -4, -5
+FAKHARI2017, CHAI2018, HU2019, LIANG2014 = 0, 1, 2, 3
+FP32, FP16_DEV, BF16_DEV = 0, 1, 2
+STORAGE = {"fp32": FP32, "fp16": FP16_DEV, "bf16": BF16_DEV}
+
+
+class PflbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("pflb error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("family", ctypes.c_int32), ("storage", ctypes.c_int32), ("bc_y", ctypes.c_int32),
+        ("visc_interp", ctypes.c_int32), ("freeze_phi", ctypes.c_int32), ("obs_capacity", ctypes.c_int32),
+        ("phi_H", ctypes.c_double), ("phi_L", ctypes.c_double),
+        ("rho_H", ctypes.c_double), ("rho_L", ctypes.c_double),
+        ("nu_H", ctypes.c_double), ("nu_L", ctypes.c_double),
+        ("sigma", ctypes.c_double), ("W", ctypes.c_double), ("M", ctypes.c_double),
+        ("lambda_hybrid", ctypes.c_double), ("eta_ch", ctypes.c_double),
+        ("gravity", ctypes.c_double * 3), ("force_density", ctypes.c_double * 3),
+        ("lundgren_A", ctypes.c_double), ("wall_u", ctypes.c_double * 2),
+        ("grad_eps", ctypes.c_double),
+    ]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [
+        ("step", ctypes.c_int64), ("sum_phi", ctypes.c_double), ("vol_smooth", ctypes.c_double),
+        ("vol_count", ctypes.c_int64), ("ke", ctypes.c_double), ("phi_max", ctypes.c_double),
+        ("phi_min", ctypes.c_double), ("centroid", ctypes.c_double * 3),
+        ("status", ctypes.c_int32), ("pad", ctypes.c_int32),
+    ]
+
+    def to_dict(self):
+        return dict(step=self.step, sum_phi=self.sum_phi, vol_smooth=self.vol_smooth,
+                    vol_count=self.vol_count, ke=self.ke, phi_max=self.phi_max,
+                    phi_min=self.phi_min, centroid=list(self.centroid), status=self.status)
+
+
+_lib = None
+
+# Every entry point of include/pflb.h with its ctypes signature.
+SIGNATURES = {
+    "pflb_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "pflb_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pflb_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "pflb_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "pflb_observables": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Obs)]),
+    "pflb_obs_history": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Obs), ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_int32)]),
+    "pflb_get_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pflb_state_floats": (ctypes.c_int64, [ctypes.c_void_p]),
+    "pflb_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "pflb_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "pflb_step_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "pflb_bytes_per_update": (ctypes.c_double, [ctypes.c_void_p]),
+    "pflb_set_chunk": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "pflb_lattice": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.c_void_p, ctypes.c_void_p]),
+    "pflb_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "pflb_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+}
+
+
+def load_library(path=None):
+    """Load libpflb.so (built in-tree by build.build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("libpflb.so not found at %s: build it first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(buf):
+    """Device or host address of a buffer (torch tensor, numpy array or int)."""
+    if buf is None:
+        return None
+    if isinstance(buf, int):
+        return buf
+    if hasattr(buf, "data_ptr"):
+        if not buf.is_contiguous():
+            raise ValueError("buffer must be contiguous")
+        return buf.data_ptr()
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return buf.ctypes.data
+    raise TypeError("unsupported buffer type %r" % type(buf))
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_params(d):
+    """Fill the C parameter struct from a dictionary (keys as in cases.params)."""
+    p = Params()
+    p.dim = int(d["dim"])
+    p.nx, p.ny = int(d["nx"]), int(d["ny"])
+    p.nz = int(d.get("nz", 1)) if p.dim == 3 else 1
+    p.family = int(d.get("family", 0))
+    st = d.get("storage", FP32)
+    p.storage = STORAGE[st] if isinstance(st, str) else int(st)
+    p.bc_y = int(d.get("bc_y", 0))
+    p.visc_interp = int(d.get("visc_interp", 0))
+    p.freeze_phi = int(d.get("freeze_phi", 0))
+    p.obs_capacity = int(d.get("obs_capacity", 64))
+    for k in ("phi_H", "phi_L", "rho_H", "rho_L", "nu_H", "nu_L", "sigma", "W", "M",
+              "lambda_hybrid", "eta_ch", "lundgren_A", "grad_eps"):
+        setattr(p, k, float(d.get(k, {"phi_H": 1.0, "phi_L": 0.0, "lambda_hybrid": 0.9,
+                                        "eta_ch": 1.0, "grad_eps": 1e-12}.get(k, 0.0))))
+    g = d.get("gravity", (0.0, 0.0, 0.0))
+    fd = d.get("force_density", (0.0, 0.0, 0.0))
+    wu = d.get("wall_u", (0.0, 0.0))
+    for k in range(3):
+        p.gravity[k] = float(g[k]) if k < len(g) else 0.0
+        p.force_density[k] = float(fd[k]) if k < len(fd) else 0.0
+    p.wall_u[0], p.wall_u[1] = float(wu[0]), float(wu[1])
+    return p
+
+
+class Sim:
+    """One PF-LB domain on the current CUDA device (a pflb_handle)."""
+
+    def __init__(self, params, stream=None):
+        self.lib = load_library()
+        self.params = dict(params)
+        self._p = make_params(params)
+        h = ctypes.c_void_p()
+        rc = self.lib.pflb_create(ctypes.byref(self._p), _stream(stream), ctypes.byref(h))
+        self.h = h
+        if rc != PFLB_OK:
+            msg = self.lib.pflb_last_error(h).decode() if h.value else "create failed"
+            self.lib.pflb_destroy(h)
+            self.h = ctypes.c_void_p()
+            raise PflbError(rc, msg)
+        self.dim = self._p.dim
+        self.shape = (self._p.ny, self._p.nx) if self.dim == 2 else (self._p.nz, self._p.ny, self._p.nx)
+        self.N = int(np.prod(self.shape))
+
+    def _check(self, rc):
+        if rc != PFLB_OK:
+            raise PflbError(rc, self.lib.pflb_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            self.lib.pflb_destroy(self.h)
+        self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, phi0, u0=None):
+        """phi0 (N) and u0 (d*N, or None): host numpy float32 or device tensors."""
+        if isinstance(phi0, np.ndarray):
+            phi0 = np.ascontiguousarray(phi0, dtype=np.float32)
+        if isinstance(u0, np.ndarray):
+            u0 = np.ascontiguousarray(u0, dtype=np.float32)
+        self._keep = (phi0, u0)
+        return self._check(self.lib.pflb_init(self.h, _ptr(phi0), _ptr(u0)))
+
+    def step(self, n=1):
+        return self._check(self.lib.pflb_step(self.h, int(n)))
+
+    def sync(self):
+        return self._check(self.lib.pflb_sync(self.h))
+
+    @property
+    def step_count(self):
+        return int(self.lib.pflb_step_count(self.h))
+
+    def set_chunk(self, c):
+        return self._check(self.lib.pflb_set_chunk(self.h, int(c)))
+
+    def bytes_per_update(self):
+        return float(self.lib.pflb_bytes_per_update(self.h))
+
+    def observables(self):
+        o = Obs()
+        self._check(self.lib.pflb_observables(self.h, ctypes.byref(o)))
+        return o.to_dict()
+
+    def history(self, n):
+        arr = (Obs * max(int(n), 1))()
+        w = ctypes.c_int32()
+        self._check(self.lib.pflb_obs_history(self.h, arr, int(n), ctypes.byref(w)))
+        return [arr[i].to_dict() for i in range(w.value)]
+
+    def fields(self, phi=None, u=None, p=None):
+        """Fill the given buffers (host or device); with none given, return
+        host numpy arrays (phi, u, p) shaped like the domain."""
+        if phi is None and u is None and p is None:
+            phi = np.empty(self.shape, dtype=np.float32)
+            u = np.empty((self.dim,) + self.shape, dtype=np.float32)
+            p = np.empty(self.shape, dtype=np.float32)
+        self._check(self.lib.pflb_get_fields(self.h, _ptr(phi), _ptr(u), _ptr(p)))
+        return phi, u, p
+
+    def state_floats(self):
+        return int(self.lib.pflb_state_floats(self.h))
+
+    def save(self, out=None):
+        """Canonical FP32 state (host numpy array unless a buffer is given)."""
+        if out is None:
+            out = np.empty(self.state_floats(), dtype=np.float32)
+        self._check(self.lib.pflb_save(self.h, _ptr(out)))
+        return out
+
+    def load(self, state):
+        if isinstance(state, np.ndarray):
+            state = np.ascontiguousarray(state, dtype=np.float32)
+        return self._check(self.lib.pflb_load(self.h, _ptr(state)))
+
+
+def lattice(dim, which):
+    """(e (Q x 3) int array, w (Q) array) of a lattice in canonical order."""
+    lib = load_library()
+    q = ctypes.c_int32()
+    e = np.zeros(3 * 27, dtype=np.int32)
+    w = np.zeros(27, dtype=np.float64)
+    rc = lib.pflb_lattice(int(dim), int(which), ctypes.byref(q), e.ctypes.data, w.ctypes.data)
+    if rc != PFLB_OK:
+        raise PflbError(rc, "pflb_lattice")
+    return e[: 3 * q.value].reshape(q.value, 3), w[: q.value]

@@ -1,0 +1,108 @@
+"""Parity at the full sizes of the benchmark workloads, in the launch
+configuration the benchmark uses (default block chunking).
+
+  * 2D Rayleigh-Taylor, 256 x 1024, walls, Atwood 0.5, all four families:
+    whole-field comparison with the FP64 oracle after 50 steps.
+  * 3D droplet-laden turbulence, 512^3, 200 droplets, Fakhari2017, FP32 and
+    FP16 storage: one step checked at sampled cells (each recomputed by the
+    oracle on a periodic patch of radius 2 around the cell from the GPU's
+    own previous state), plus sum(phi) conservation over 20 steps.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2511_11360_gb300 import cases as C
+from paper_2511_11360_gb300 import pflb
+
+from gpu_common import compare_fields, make_sim, oracle_start, require_gpu, torch
+
+pytestmark = pytest.mark.gpu
+
+FAMS = list(C.FAMILIES)
+FID = [C.FAMILY_NAMES[f] for f in FAMS]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+@pytest.mark.parametrize("fam", FAMS, ids=FID)
+def test_rayleigh_taylor_256x1024(fam):
+    P, phi, u = C.rayleigh_taylor_2d(nx=256, ny=1024, family=fam)
+    sim = make_sim(P, phi, u)
+    sim.step(50)
+    sim.sync()
+    st = O.run(P, oracle_start(P, phi, u), 50)
+    compare_fields(sim, P, st, 1e-5, 1e-5)
+
+
+@pytest.fixture(scope="module")
+def hit512():
+    P, phi, u, _ = C.hit_droplets_3d_torch(n=512, device="cuda")
+    return P, phi, u
+
+
+def _gather_patches(state, n, cells, r):
+    """(ncells, nq, 2r+1, 2r+1, 2r+1) float64 patches of a canonical device
+    state (nq, n, n, n), periodic."""
+    nq = state.shape[0]
+    off = torch.arange(-r, r + 1, device=state.device)
+    out = []
+    for (x, y, z) in cells:
+        ix = (x + off) % n
+        iy = (y + off) % n
+        iz = (z + off) % n
+        p = state[:, iz[:, None, None], iy[None, :, None], ix[None, None, :]]
+        out.append(p.double().cpu().numpy())
+    return np.stack(out)
+
+
+@pytest.mark.parametrize("storage,tol", [(0, 2e-6), (1, 1.5e-3)], ids=["fp32", "fp16"])
+def test_hit_512_sampled_one_step(hit512, storage, tol):
+    P, phi, u = hit512
+    n = P["nx"]
+    sim = pflb.Sim(dict(P, storage=storage))
+    sim.init(phi.contiguous(), u.contiguous())
+    sim.step(3)
+    nf = sim.state_floats() // (n ** 3)
+    before = torch.empty(sim.state_floats(), device="cuda")
+    sim.save(before)
+    before = before.view(nf, n, n, n)
+    rng = np.random.default_rng(11)
+    cells = [tuple(int(v) for v in rng.integers(0, n, size=3)) for _ in range(48)]
+    # include block seams and the periodic wrap
+    cells += [(0, 0, 0), (n - 1, n - 1, n - 1), (31, 7, 63), (32, 8, 64), (511, 0, 255)]
+    r = 2
+    patches = _gather_patches(before, n, cells, r)
+    sim.step(1)
+    sim.sync()
+    after = torch.empty(sim.state_floats(), device="cuda")
+    sim.save(after)
+    after = after.view(nf, n, n, n)
+    lg, lf, _ = O.lattices_for(3)
+    Pp = dict(P, nx=2 * r + 1, ny=2 * r + 1, nz=2 * r + 1)
+    scale = float(before.abs().max().item())
+    worst = 0.0
+    for i, (x, y, z) in enumerate(cells):
+        st = O.State(patches[i, : lg.Q].copy(), patches[i, lg.Q: lg.Q + lf.Q].copy(), None, 3)
+        g, f = O.step_at_cells(Pp, st, [(r, r, r)])
+        want = np.concatenate([g[:, 0], f[:, 0]])
+        got = after[:, z, y, x].double().cpu().numpy()
+        worst = max(worst, float(np.max(np.abs(got - want))) / scale)
+    assert worst <= tol, worst
+
+
+def test_hit_512_conserves_sum_phi(hit512):
+    P, phi, u = hit512
+    sim = pflb.Sim(dict(P, obs_capacity=64))
+    sim.init(phi.contiguous(), u.contiguous())
+    s0 = sim.observables()
+    sim.step(20)
+    s1 = sim.observables()
+    assert s1["status"] == 0
+    assert abs(s1["sum_phi"] / s0["sum_phi"] - 1) < 1e-6
+    # vol_count at t = 0 equals the count of the input field
+    assert s0["vol_count"] == int((phi > 0.5).sum().item())

@@ -1,0 +1,234 @@
+"""GPU (CUDA, through the C ABI) vs FP64 oracle parity on identical seeded inputs.
+
+Bars (Reading R15 metric, max|a - b| / max|b|):
+  * one step from the same canonical state: populations within FP32 round-off
+    (FP16/BF16 storage: within the 16-bit encoding of the written deviation);
+  * 1000 steps on laminar cases, ragged grids spanning several tiles and
+    chunks, all four families, periodic / resting walls / moving walls / 3D:
+    phi and u within 1e-5;
+  * observables, sum(phi) conservation, save/load continuation, instability
+    status.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2511_11360_gb300 import cases as C
+from paper_2511_11360_gb300 import pflb
+
+from gpu_common import as_f32, compare_fields, make_sim, oracle_start, rel_linf, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+FAMS = list(C.FAMILIES)
+FID = [C.FAMILY_NAMES[f] for f in FAMS]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+# --------------------------------------------------------------------------- cases
+def small_case(kind, fam):
+    """Small ragged grids: several tiles / chunks at the chunk sizes used."""
+    if kind == "2d":
+        P, phi, u = C.droplet_in_vortex_2d(nx=150, ny=37, R=9.0, W=4.0, family=fam)
+        P.update(rho_H=2.0, rho_L=1.0, nu_L=0.05)
+        return P, phi, u, 4
+    if kind == "2d_walls":
+        P, phi, u = C.rayleigh_taylor_2d(nx=40, ny=76, W=4.0, family=fam)
+        return P, phi, u, 8
+    if kind == "2d_moving":
+        P, phi, u = C.shear_instance(36, fam, Ca=0.2, M=0.05, W=4)
+        return P, phi, u, 5
+    if kind == "3d":
+        P, phi, u = C.droplet_in_tgv_3d(nx=35, ny=11, nz=9, R=4.0, W=3.0, family=fam)
+        P.update(rho_H=2.0, rho_L=1.0, nu_L=0.05)
+        return P, phi, u, 3
+    raise ValueError(kind)
+
+
+def laminar_case(kind, fam):
+    if kind == "2d":
+        P, phi, u = C.droplet_in_vortex_2d(nx=150, ny=70, R=14.0, W=4.0, family=fam)
+        P.update(rho_H=2.0, rho_L=1.0, nu_L=0.05)
+        return P, phi, u, 8
+    if kind == "2d_walls":
+        P, phi, u = C.rayleigh_taylor_2d(nx=48, ny=96, W=4.0, family=fam)
+        return P, phi, u, 16
+    if kind == "2d_moving":
+        P, phi, u = C.shear_instance(48, fam, Ca=0.2, M=0.05, W=4)
+        return P, phi, u, 8
+    if kind == "3d":
+        P, phi, u = C.droplet_in_tgv_3d(nx=40, ny=20, nz=18, R=6.0, W=3.0, family=fam)
+        P.update(rho_H=2.0, rho_L=1.0, nu_L=0.05)
+        return P, phi, u, 4
+    raise ValueError(kind)
+
+
+def canon_oracle(P, st):
+    return O.pack_state(P, st)
+
+
+# ------------------------------------------------------------ one-step parity
+STORAGE_TOL = {0: 2e-6, 1: 1.5e-3, 2: 1.2e-2}   # relative to max |population|
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2], ids=["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("kind", ["2d", "2d_walls", "2d_moving", "3d"])
+@pytest.mark.parametrize("fam", FAMS, ids=FID)
+def test_one_step_canonical_parity(fam, kind, storage):
+    """Init and two steps (an even and an odd AA step): the GPU's canonical
+    state equals the oracle's step from the GPU's own previous state."""
+    P, phi, u, chunk = small_case(kind, fam)
+    sim = make_sim(P, phi, u, storage=storage, chunk=chunk)
+    tol = STORAGE_TOL[storage]
+    s0 = sim.save().astype(np.float64)
+    ref0 = canon_oracle(P, oracle_start(P, phi, u)).reshape(-1)
+    scale = np.max(np.abs(ref0))
+    assert np.max(np.abs(s0 - ref0)) <= tol * scale
+    prev = s0
+    for k in range(2):
+        sim.step(1)
+        sim.sync()
+        got = sim.save().astype(np.float64)
+        st = O.unpack_state(P, prev, t=k)
+        want = canon_oracle(P, O.step(P, st)).reshape(-1)
+        err = np.max(np.abs(got - want)) / scale
+        assert err <= tol, (k, err)
+        prev = got
+
+
+# ------------------------------------------------------- 1000-step parity
+@pytest.mark.parametrize("kind", ["2d", "2d_walls", "2d_moving", "3d"])
+@pytest.mark.parametrize("fam", FAMS, ids=FID)
+def test_laminar_1000_steps_fp32(fam, kind):
+    """phi and u after 1000 steps within 1e-5 (relative L-infinity) of the FP64
+    oracle run from the same (float32-rounded) inputs."""
+    P, phi, u, chunk = laminar_case(kind, fam)
+    sim = make_sim(P, phi, u, chunk=chunk)
+    sim.step(1000)
+    sim.sync()
+    st = O.run(P, oracle_start(P, phi, u), 1000)
+    compare_fields(sim, P, st, 1e-5, 1e-5)
+
+
+# ---------------------------------------------------------------- observables
+@pytest.mark.parametrize("fam", FAMS, ids=FID)
+def test_observables_match_oracle(fam):
+    P, phi, u, chunk = laminar_case("2d", fam)
+    sim = make_sim(P, phi, u, chunk=chunk)
+    sim.step(200)
+    got = sim.observables()
+    st = O.run(P, oracle_start(P, phi, u), 200)
+    want = O.observables(P, st)
+    assert got["step"] == 200 and got["status"] == 0
+    assert abs(got["sum_phi"] / want["sum_phi"] - 1) < 1e-6
+    assert abs(got["vol_smooth"] / want["vol_smooth"] - 1) < 1e-6
+    assert abs(got["ke"] / want["ke"] - 1) < 1e-4
+    assert abs(got["phi_max"] - want["phi_max"]) < 1e-5
+    assert abs(got["phi_min"] - want["phi_min"]) < 1e-5
+    for k in range(2):
+        assert abs(got["centroid"][k] - want["centroid"][k]) < 1e-3
+    # The count is an integer decided in FP32 on the GPU: recount the GPU's own
+    # FP32 phi in FP32.
+    gphi, _, _ = sim.fields()
+    assert got["vol_count"] == int(np.count_nonzero(gphi > np.float32(0.5)))
+
+
+@pytest.mark.parametrize("fam", FAMS, ids=FID)
+@pytest.mark.parametrize("kind", ["2d", "3d"])
+def test_sum_phi_conserved_fp32(fam, kind):
+    """Sum phi on a periodic domain drifts only by FP32 storage rounding:
+    below 1e-6 relative over 1000 steps (the oracle holds it to 1e-13)."""
+    P, phi, u, chunk = laminar_case(kind, fam)
+    sim = make_sim(P, phi, u, chunk=chunk, obs_capacity=2048)
+    s0 = sim.observables()["sum_phi"]
+    sim.step(1000)
+    hist = sim.history(1000)
+    assert len(hist) == 1000 and hist[0]["step"] == 0
+    s1 = sim.observables()["sum_phi"]
+    assert abs(s1 / s0 - 1) < 1e-6
+    drift = max(abs(h["sum_phi"] / s0 - 1) for h in hist)
+    assert drift < 1e-6
+
+
+def test_history_equals_observables_of_that_state():
+    P, phi, u, chunk = laminar_case("2d", C.FAKHARI2017)
+    sim = make_sim(P, phi, u, chunk=chunk)
+    sim.step(5)
+    now = sim.observables()
+    sim.step(1)
+    last = sim.history(1)[-1]
+    assert last["step"] == 5
+    for k in ("sum_phi", "vol_smooth", "ke", "phi_max", "phi_min"):
+        assert math.isclose(last[k], now[k], rel_tol=1e-12, abs_tol=1e-15), k
+    assert last["vol_count"] == now["vol_count"]
+
+
+# ------------------------------------------------------------- state handling
+@pytest.mark.parametrize("fam", FAMS, ids=FID)
+def test_save_load_continues_bitwise(fam):
+    P, phi, u, chunk = small_case("2d_walls", fam)
+    a = make_sim(P, phi, u, chunk=chunk)
+    a.step(11)
+    blob = a.save()
+    a.step(10)
+    pa = a.fields()
+    b = make_sim(P, phi, u, chunk=chunk)   # even parity, step 0
+    b.load(blob)
+    b.step(10)
+    pb = b.fields()
+    for x, y in zip(pa, pb):
+        assert np.array_equal(x, y)
+
+
+def test_instability_is_reported():
+    P, phi, u, chunk = small_case("2d", C.FAKHARI2017)
+    sim = make_sim(P, phi, u, chunk=chunk)
+    blob = sim.save()
+    blob[5] = np.nan
+    sim.load(blob)
+    sim.step(2)
+    with pytest.raises(pflb.PflbError) as ei:
+        sim.sync()
+    assert ei.value.code == pflb.PFLB_EUNSTABLE
+
+
+def test_device_buffers_accepted():
+    """Inputs and outputs may be device tensors (torch supplies the memory)."""
+    import torch
+    P, phi, u, chunk = small_case("3d", C.FAKHARI2017)
+    d = dict(P)
+    sim = pflb.Sim(d, stream=torch.cuda.current_stream())
+    tphi = torch.tensor(as_f32(phi), device="cuda")
+    tu = torch.tensor(as_f32(u), device="cuda")
+    sim.init(tphi, tu)
+    sim.step(3)
+    ophi = torch.empty_like(tphi)
+    ou = torch.empty_like(tu)
+    op = torch.empty_like(tphi)
+    sim.fields(ophi, ou, op)
+    hphi, hu, hp = sim.fields()
+    assert np.array_equal(ophi.cpu().numpy(), hphi)
+    assert np.array_equal(ou.cpu().numpy(), hu)
+    dev_state = torch.empty(sim.state_floats(), device="cuda")
+    sim.save(dev_state)
+    assert np.array_equal(dev_state.cpu().numpy(), sim.save())
+
+
+# ------------------------------------------------------- 16-bit storage error
+@pytest.mark.parametrize("storage,tol", [(1, 5e-3), (2, 4e-2)], ids=["fp16", "bf16"])
+def test_16bit_storage_error_vs_oracle(storage, tol):
+    """FP16/BF16 deviation storage, FP32 arithmetic: error of phi and u against
+    the FP64 oracle after 200 steps of the 3D droplet-in-TGV case."""
+    P, phi, u, chunk = laminar_case("3d", C.FAKHARI2017)
+    sim = make_sim(P, phi, u, storage=storage, chunk=chunk)
+    sim.step(200)
+    st = O.run(P, oracle_start(P, phi, u), 200)
+    e_phi, e_u = compare_fields(sim, P, st, tol, 10 * tol)
+    print("storage %d: phi rel Linf %.3e  u rel Linf %.3e" % (storage, e_phi, e_u))
