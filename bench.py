@@ -62,7 +62,7 @@ class Clocks:
         self.proc = None
         self.path = None
 
-    def start(self):
+    def start(self, wait=5.0):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -75,6 +75,13 @@ class Clocks:
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # let the sampler reach its polling loop before the timed region
+        t0 = time.time()
+        while time.time() - t0 < wait:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.05)
 
     def stop(self):
         if self.proc is None:
@@ -189,24 +196,32 @@ def cpu_baseline(seconds_target=15.0):
 
 
 def reference_main(args):
+    """The FP64 oracle as it stands, timed on the host cores: each step is one
+    oracle step of a periodic 64^3 sample of the same recipe."""
     rank, world, local = _dist()
     if rank != 0:
         return 0
-    per = []
+    import oracle as O
+    from paper_2511_11360_gb300 import cases as C
+    n = 64
+    P, phi, u, _ = C.hit_droplets_3d(n=n, count=2, R=16.0, W=4.0, We=5.0, seed=C.DEFAULT_SEED)
+    st = O.init_state(P, phi, u)
     for _ in range(args.warmup):
-        cpu_baseline(seconds_target=2.0)
+        st = O.step(P, st)
     t0 = time.perf_counter()
-    vals = []
     for _ in range(args.steps):
-        vals.append(cpu_baseline(seconds_target=4.0))
+        st = O.step(P, st)
     dt = time.perf_counter() - t0
-    value = statistics.median(v["value"] for v in vals)
+    value = n ** 3 * args.steps / dt / 1e9
+    sample = ("%d oracle steps of a 64^3 periodic box of the same recipe (2 droplets R=16, W=4, "
+              "solenoidal u), numpy float64, single thread" % args.steps)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / max(args.steps, 1) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD + " (bounded 64^3 sample on host cores)"},
-            "cpu_baseline": dict(vals[-1], value=value),
+            "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -215,10 +230,11 @@ def reference_main(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
@@ -246,12 +262,14 @@ def main():
     pflb.load_library()
 
     n = args.n
-    P, phi, u, centres = C.hit_droplets_3d_torch(n=n, seed=C.DEFAULT_SEED + rank)
+    count = max(1, int(round(200 * (n / 512.0) ** 3)))
+    P, phi, u, centres = C.hit_droplets_3d_torch(n=n, count=count, seed=C.DEFAULT_SEED + rank)
     cells = n ** 3
     peak, peak_kind = _peaks()
 
-    # ---- FP32, device-resident inputs
-    sim = pflb.Sim(dict(P, obs_capacity=4), stream=torch.cuda.current_stream())
+    # ---- primary storage (FP32 by default), device-resident inputs
+    storage = pflb.STORAGE[args.storage]
+    sim = pflb.Sim(dict(P, storage=storage, obs_capacity=4), stream=torch.cuda.current_stream())
     sim.init(phi, u)
     bytes_lu = sim.bytes_per_update()
     clocks = Clocks(local)
@@ -277,6 +295,8 @@ def main():
     variants = {}
     if not args.no_variants:
         for name, st in (("fp16_storage", 1), ("bf16_storage", 2)):
+            if st == storage:
+                continue
             s2 = pflb.Sim(dict(P, storage=st, obs_capacity=4), stream=torch.cuda.current_stream())
             s2.init(phi, u)
             b2 = s2.bytes_per_update()
@@ -294,7 +314,8 @@ def main():
     del phi, u
     torch.cuda.empty_cache()
     e2e_steps = max(args.steps // 2, 5)
-    te = _max_over_ranks(e2e_run(dict(P, obs_capacity=4), phi_h.numpy(), u_h.numpy(), e2e_steps, world), world)
+    te = _max_over_ranks(e2e_run(dict(P, storage=storage, obs_capacity=4), phi_h.numpy(), u_h.numpy(),
+                                 e2e_steps, world), world)
     e2e = {"value": cells * e2e_steps * world / te / 1e9, "unit": "GLUPS",
            "h2d_bytes_per_step": int(4 * cells * 4 / e2e_steps),
            "d2h_bytes_per_step": int(96 + 4 * cells / e2e_steps)}
@@ -310,12 +331,12 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "cells": cells, "family": "fakhari2017",
-                   "storage": "fp32", "l2": "state %.1f GB >> 126 MB L2, no flush needed" % (
+                   "storage": args.storage, "l2": "state %.1f GB >> 126 MB L2, no flush needed" % (
                        bytes_lu * cells / 2 / 1e9),
                    "bytes_per_lu": bytes_lu, "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "step_kernel<fakhari,3D,f32>"},
+                     "kernel": "step_kernel<fakhari,3D,%s>" % args.storage},
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": ck,

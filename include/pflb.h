@@ -58,9 +58,10 @@ typedef enum pflb_family {
 } pflb_family;
 
 /* Population storage in device memory. Arithmetic is always FP32. The 16-bit
- * forms store (value - w_a * c_a) / w_a with c_a = (phi_H + phi_L)/2 for g and
- * 0 for f (w_a = 1 where a weight is zero): the deviation from the rest state
- * scaled by the lattice weight. */
+ * forms store (value - w_a c) / s_a: the deviation from the rest state (c =
+ * (phi_H + phi_L)/2 for g, 0 for f; w_a = 1 where the weight is zero) scaled by
+ * s_a, the power of two nearest w_a (exact both ways, so only the 16-bit
+ * rounding of the deviation is lost). */
 typedef enum pflb_storage {
   PFLB_FP32 = 0,
   PFLB_FP16_DEV = 1,
@@ -94,7 +95,9 @@ typedef struct pflb_params {
   double force_density[3]; /* uniform force density added to F_b */
   double lundgren_A;    /* linear forcing F = A rho u (turbulence driver) */
   double wall_u[2];     /* x velocity of the bottom and top wall (bc_y = 2) */
-  double grad_eps;      /* |grad phi| below which the interface normal is 0 */
+  double grad_eps;      /* |grad phi| below which the interface normal, and the
+                           conservative counter flux, are 0 (1e-6: the FP32
+                           noise floor of a gradient of phi = O(1)) */
 } pflb_params;
 
 /* Bookkeeping of one state: sums over all cells of its macroscopic fields. */

@@ -108,7 +108,7 @@ def default_params(**kw):
              lambda_hybrid=0.9,      # Sec. III: lambda = 0.9 for Hu2019
              eta_ch=1.0,             # Reading R12
              gravity=(0.0, 0.0, 0.0), force_density=(0.0, 0.0, 0.0),
-             lundgren_A=0.0, wall_u=(0.0, 0.0), grad_eps=1e-12,
+             lundgren_A=0.0, wall_u=(0.0, 0.0), grad_eps=1e-6,
              freeze_phi=0)
     p.update(kw)
     return p
@@ -305,8 +305,10 @@ def feq_pressure(lat, p, rho, u):
 
 def source_conservative(P, lat, phi, grad_phi):
     """G = w e . [ sqrt(2 beta/kappa) (phi_H - phi)(phi - phi_L) grad(phi)/|grad(phi)| ]
-    Eq. (fakhari_G_modified). Reading R6: the unit normal is taken as zero where
-    |grad phi|^2 < eps^2."""
+    Eq. (fakhari_G_modified). Reading R6: the unit normal is undefined where
+    the gradient vanishes; it is taken as zero where |grad phi| < eps, with
+    eps = 1e-6 by default (below that a gradient of phi = O(1) is at the FP32
+    noise floor and its direction carries no information)."""
     c = derived(P)
     k = np.sqrt(2.0 * c["beta"] / c["kappa"])
     g2 = _udotu(grad_phi)

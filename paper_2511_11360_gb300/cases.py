@@ -29,7 +29,7 @@ def params(**kw):
              phi_H=1.0, phi_L=0.0, rho_H=1.0, rho_L=1.0, nu_H=0.1, nu_L=0.1,
              visc_interp=0, sigma=1e-3, W=4.0, M=0.1, lambda_hybrid=0.9,
              eta_ch=1.0, gravity=(0.0, 0.0, 0.0), force_density=(0.0, 0.0, 0.0),
-             lundgren_A=0.0, wall_u=(0.0, 0.0), grad_eps=1e-12, freeze_phi=0)
+             lundgren_A=0.0, wall_u=(0.0, 0.0), grad_eps=1e-6, freeze_phi=0)
     p.update(kw)
     return p
 
@@ -99,11 +99,12 @@ def droplet_in_vortex_2d(nx=100, ny=70, R=14.0, W=4.0, u0=0.02, family=FAKHARI20
 
 
 def rayleigh_taylor_2d(nx=256, ny=1024, At=0.5, Re=3000.0, Pe=1000.0, W=5.0,
-                       amp=0.1, family=FAKHARI2017, **kw):
+                       amp=0.1, family=FAKHARI2017, heavy_on_top=True, **kw):
     """Rayleigh-Taylor instability, Sec. III C, with the heavier fluid above the
     perturbed interface y_t = 2 L0 + amp L0 cos(2 pi x / L0), L0 = nx.
     sqrt(g L0) = 0.04, sigma = 5e-5; At, Re and Pe fix rho_H/rho_L, nu and M.
-    Periodic in x, no-slip walls in y."""
+    Periodic in x, no-slip walls in y. heavy_on_top=False gives the stably
+    stratified counterpart (the perturbed interface oscillates and decays)."""
     L0 = nx
     g = 0.04 ** 2 / L0
     rho_L = 1.0
@@ -112,7 +113,7 @@ def rayleigh_taylor_2d(nx=256, ny=1024, At=0.5, Re=3000.0, Pe=1000.0, W=5.0,
     M = L0 * math.sqrt(g * L0) / Pe
     x, y = _grid((ny, nx))
     yt = 0.5 * ny + amp * L0 * np.cos(2 * math.pi * (x + 0.5) / L0)
-    phi = _tanh_profile((y + 0.5) - yt, W)
+    phi = _tanh_profile(((y + 0.5) - yt) * (1.0 if heavy_on_top else -1.0), W)
     u = np.zeros((2, ny, nx))
     P = params(dim=2, nx=nx, ny=ny, family=family, bc_y=1, rho_H=rho_H, rho_L=rho_L,
                nu_H=nu, nu_L=nu, sigma=5e-5, W=W, M=M, gravity=(0.0, -g, 0.0))
@@ -227,13 +228,16 @@ def droplet_field(n, centres, R, W, dtype=np.float64):
     return phi
 
 
-def hit_droplets_3d(n=512, count=200, R=16.0, W=4.0, We=5.0, u_rms=0.04, nu=0.006,
-                    M=0.01, lundgren_A=1e-4, seed=DEFAULT_SEED, family=FAKHARI2017,
+def hit_droplets_3d(n=512, count=200, R=16.0, W=4.0, We=5.0, u_rms=0.04, nu=0.02,
+                    M=0.05, lundgren_A=1e-4, seed=DEFAULT_SEED, family=FAKHARI2017,
                     dtype=np.float64, with_velocity=True, **kw):
     """Droplet-laden forced isotropic turbulence, Sec. IV: periodic cube,
     density ratio 1, sigma = rho_H u_rms^2 (2R) / We (Sec. IV definition of We),
     linear forcing coefficient A (the paper's stochastic forcing is replaced by
-    linear forcing F = A rho u). The velocity is a random solenoidal field."""
+    linear forcing F = A rho u). The velocity is a random solenoidal field.
+    nu = 0.02 and M = 0.05 (tau = 0.56, tau_phi = 0.65): with single-relaxation
+    BGK the paper's nu = 0.006, M = 0.01 (it used MRT) blow up within a few
+    hundred steps from this start, in the FP64 oracle as on the GPU."""
     centres = place_droplets(n, count, R, W, seed=seed)
     phi = droplet_field(n, centres, R, W, dtype=dtype)
     u = None
@@ -246,18 +250,21 @@ def hit_droplets_3d(n=512, count=200, R=16.0, W=4.0, We=5.0, u_rms=0.04, nu=0.00
     return P, phi, u, centres
 
 
-def droplet_in_tgv_3d(n=32, R=6.0, W=4.0, u0=0.02, family=FAKHARI2017, nx=None, ny=None, nz=None, **kw):
-    """Droplet of radius R at the centre of a Taylor-Green vortex,
-    u = u0 (sin kx cos ky cos kz, -cos kx sin ky cos kz, 0)."""
+def droplet_in_tgv_3d(n=32, R=6.0, W=4.0, u0=0.02, family=FAKHARI2017, nx=None, ny=None, nz=None,
+                      centre=(0.5, 0.5, 0.5), phase=(0.0, 0.0, 0.0), **kw):
+    """Droplet of radius R (centre given as fractions of the box) in a
+    Taylor-Green vortex u = u0 (sin X cos Y cos Z, -(kx/ky) cos X sin Y cos Z, 0),
+    X = kx x + phase_x etc. (divergence free for any phases)."""
     nx = nx or n
     ny = ny or n
     nz = nz or n
     x, y, z = _grid((nz, ny, nx))
-    r = np.sqrt((x - 0.5 * nx) ** 2 + (y - 0.5 * ny) ** 2 + (z - 0.5 * nz) ** 2)
+    r = np.sqrt((x - centre[0] * nx) ** 2 + (y - centre[1] * ny) ** 2 + (z - centre[2] * nz) ** 2)
     phi = _tanh_profile(R - r, W)
     kx, ky, kz = 2 * math.pi / nx, 2 * math.pi / ny, 2 * math.pi / nz
-    u = np.stack([u0 * np.sin(kx * x) * np.cos(ky * y) * np.cos(kz * z),
-                  -u0 * (kx / ky) * np.cos(kx * x) * np.sin(ky * y) * np.cos(kz * z),
+    X, Y, Z = kx * x + phase[0], ky * y + phase[1], kz * z + phase[2]
+    u = np.stack([u0 * np.sin(X) * np.cos(Y) * np.cos(Z),
+                  -u0 * (kx / ky) * np.cos(X) * np.sin(Y) * np.cos(Z),
                   np.zeros_like(x)])
     P = params(dim=3, nx=nx, ny=ny, nz=nz, family=family, W=W, M=0.1, sigma=1e-3,
                nu_H=tau_to_nu(0.8), nu_L=tau_to_nu(0.8))
@@ -363,8 +370,8 @@ def droplet_field_torch(n, centres, R, W, device="cuda"):
     return phi
 
 
-def hit_droplets_3d_torch(n=512, count=200, R=16.0, W=4.0, We=5.0, u_rms=0.04, nu=0.006,
-                          M=0.01, lundgren_A=1e-4, seed=DEFAULT_SEED, family=FAKHARI2017,
+def hit_droplets_3d_torch(n=512, count=200, R=16.0, W=4.0, We=5.0, u_rms=0.04, nu=0.02,
+                          M=0.05, lundgren_A=1e-4, seed=DEFAULT_SEED, family=FAKHARI2017,
                           device="cuda", **kw):
     """hit_droplets_3d() with the fields generated on a torch device."""
     centres = place_droplets(n, count, R, W, seed=seed)

@@ -85,7 +85,9 @@ int validate(const pflb_params* p, char* msg, size_t n) {
   if (p->nx < 1 || p->ny < 1 || p->nz < 1) return snprintf(msg, n, "sizes must be >= 1"), PFLB_EINVAL;
   if (p->dim == 2 && p->nz != 1) return snprintf(msg, n, "nz must be 1 in 2D"), PFLB_EINVAL;
   const long long N = (long long)p->nx * p->ny * p->nz;
-  if (N >= (1LL << 31)) return snprintf(msg, n, "at most 2^31 - 1 cells"), PFLB_EINVAL;
+  // Population offsets q*N + cell are 32-bit in the kernels.
+  const long long qmax = p->dim == 2 ? 9 : 19;
+  if (N * qmax >= (1LL << 32)) return snprintf(msg, n, "Q * cells must be < 2^32 (%lld cells max)", ((1LL << 32) - 1) / qmax), PFLB_EINVAL;
   if (p->family < 0 || p->family > 3) return snprintf(msg, n, "unknown family %d", p->family), PFLB_EINVAL;
   if (p->storage < 0 || p->storage > 2) return snprintf(msg, n, "unknown storage %d", p->storage), PFLB_EINVAL;
   if (p->bc_y < 0 || p->bc_y > 2) return snprintf(msg, n, "bc_y must be 0, 1 or 2"), PFLB_EINVAL;

@@ -21,12 +21,13 @@ __global__ void __launch_bounds__(256) gamma_kernel(const GammaArgs a) {
   float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < a.N;
        idx += (long long)gridDim.x * blockDim.x) {
-    float ps = 0.0f;
+    // phi* exactly as the step kernel forms it (the nonlocal families are
+    // Allen-Cahn: on D3Q7 the rest slot is zero and not read).
+    float gv[QG];
 #pragma unroll
-    for (int q = 0; q < QG; ++q) {
-      if (DIM == 3 && q == 0) continue;  // D3Q7 rest slot of the AC families is zero
-      ps += Codec<T>::load(g + (long long)q * a.N + idx, norm_w<LG>(q), P.gref);
-    }
+    for (int q = 0; q < QG; ++q)
+      gv[q] = (DIM == 3 && q == 0) ? 0.0f : pop_load<T, LG>(g + (long long)q * a.N + idx, q, P.gref);
+    const float ps = phi_star<LG, DIM == 3>(gv);
     comp_add(h1, l1, P.four_beta_over_kappa * (ps - P.phiH) * (ps - P.phiL) * (ps - P.phi0));
     comp_add(h2, l2, (P.phiH - ps) * (ps - P.phiL));
   }
@@ -103,8 +104,8 @@ __global__ void canon_kernel(const CanonArgs a) {
       float* sp = a.state + (long long)q * N + idx;
       T* gp = g + (long long)q * N + idx;
       const bool skip = (DIM == 3 && !a.ch && q == 0);
-      if (a.to_canon) *sp = skip ? 0.0f : Codec<T>::loadc(gp, norm_w<LG>(q), P.gref);
-      else if (!skip) Codec<T>::store(gp, *sp, norm_w<LG>(q), P.gref);
+      if (a.to_canon) *sp = skip ? 0.0f : pop_loadc<T, LG>(gp, q, P.gref);
+      else if (!skip) pop_store<T, LG>(gp, q, *sp, P.gref);
     }
 #pragma unroll
     for (int q = 0; q < QF; ++q) {
@@ -130,8 +131,8 @@ __global__ void canon_kernel(const CanonArgs a) {
       }
       float* sp = a.state + (long long)(QG + q) * N + idx;
       T* fp = f + (long long)slot * N + src;
-      if (a.to_canon) *sp = Codec<T>::loadc(fp, norm_w<LF>(q), 0.0f);
-      else Codec<T>::store(fp, *sp, norm_w<LF>(q), 0.0f);
+      if (a.to_canon) *sp = pop_loadc<T, LF>(fp, q, 0.0f);
+      else pop_store<T, LF>(fp, q, *sp, 0.0f);
     }
     if (a.ch) {
       for (int k = 0; k < DIM; ++k) {

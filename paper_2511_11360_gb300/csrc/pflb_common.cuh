@@ -33,9 +33,11 @@ struct D2Q9 {
     return t[a];
   }
   __host__ __device__ static constexpr int ez(int) { return 0; }
-  __host__ __device__ static constexpr float w(int a) {
-    return a == 0 ? 4.0f / 9.0f : (a < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
+  __host__ __device__ static constexpr double wx(int a) {
+    return a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
   }
+  __host__ __device__ static constexpr float w(int a) { return (float)wx(a); }
+  __host__ __device__ static constexpr float wlo(int a) { return (float)(wx(a) - (double)w(a)); }
   __host__ __device__ static constexpr int opp(int a) {
     constexpr int t[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
     return t[a];
@@ -56,7 +58,9 @@ struct D3Q7 {
     constexpr int t[7] = {0, 0, 0, 0, 0, 1, -1};
     return t[a];
   }
-  __host__ __device__ static constexpr float w(int a) { return a == 0 ? 0.0f : 1.0f / 6.0f; }
+  __host__ __device__ static constexpr double wx(int a) { return a == 0 ? 0.0 : 1.0 / 6.0; }
+  __host__ __device__ static constexpr float w(int a) { return (float)wx(a); }
+  __host__ __device__ static constexpr float wlo(int a) { return (float)(wx(a) - (double)w(a)); }
   __host__ __device__ static constexpr int opp(int a) {
     constexpr int t[7] = {0, 2, 1, 4, 3, 6, 5};
     return t[a];
@@ -77,14 +81,25 @@ struct D3Q19 {
     constexpr int t[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
     return t[a];
   }
-  __host__ __device__ static constexpr float w(int a) {
-    return a == 0 ? 1.0f / 3.0f : (a < 7 ? 1.0f / 18.0f : 1.0f / 36.0f);
+  __host__ __device__ static constexpr double wx(int a) {
+    return a == 0 ? 1.0 / 3.0 : (a < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
   }
+  __host__ __device__ static constexpr float w(int a) { return (float)wx(a); }
+  __host__ __device__ static constexpr float wlo(int a) { return (float)(wx(a) - (double)w(a)); }
   __host__ __device__ static constexpr int opp(int a) {
     constexpr int t[19] = {0, 2, 1, 4, 3, 6, 5, 8, 7, 10, 9, 12, 11, 14, 13, 16, 15, 18, 17};
     return t[a];
   }
 };
+
+// w_a * x with the weight carried as hi + lo (w = w_hi + w_lo to ~1e-16):
+// the FP32 weights alone have sum_a w_a e_a e_a = (1 + 7.45e-9) I / 3 on D2Q9
+// and D3Q19, which biases every equilibrium moment and made the momentum grow
+// by ~1e-8 per relaxation.
+template <typename L>
+__device__ __forceinline__ float wmul(int a, float x) {
+  return fmaf(L::w(a), x, L::wlo(a) * x);
+}
 
 // Lattice triple per dimension: phase field g, hydrodynamics f, stencil.
 template <int DIM> struct Lattices;
@@ -143,42 +158,65 @@ __host__ __device__ inline float key_float(unsigned int k) {
 }
 
 // ---------------------------------------------------------------------------
-// Storage codec: FP32 pass-through, or 16-bit deviation from the rest state
-// scaled by the weight: stored = (x - w c) / w (w = 1 where the weight is 0).
+// Storage codec: FP32 pass-through, or a 16-bit deviation from the rest state,
+//   stored = (x - w' c) / s,   x = stored * s + w' c,
+// with c the rest-state constant (phi_0 for g, 0 for f), w' the weight (1
+// where the weight is 0) and s the power of two nearest w' -- a scale that is
+// exact in both directions, so encode/decode adds no bias, only the 16-bit
+// rounding of the deviation.
 // ---------------------------------------------------------------------------
+template <typename L>
+__host__ __device__ constexpr float wprime(int a) {
+  return L::w(a) > 0.0f ? L::w(a) : 1.0f;
+}
+template <typename L>
+__host__ __device__ constexpr float pow2_scale(int a) {
+  // nearest power of two to w' in log scale: 2^k with 2^(k-1/2) < w' <= 2^(k+1/2)
+  float s = 1.0f;
+  const float w = wprime<L>(a);
+  while (w < s * 0.70710678f) s *= 0.5f;
+  while (w > s * 1.41421356f) s *= 2.0f;
+  return s;
+}
+
 template <typename T> struct Codec;
 template <> struct Codec<float> {
-  __device__ __forceinline__ static float load(const float* p, float, float) { return __ldg(p); }
-  __device__ __forceinline__ static float loadc(const float* p, float, float) { return *p; }
-  __device__ __forceinline__ static void store(float* p, float v, float, float) { *p = v; }
+  __device__ __forceinline__ static float ld(const float* p) { return __ldg(p); }
+  __device__ __forceinline__ static float ldc(const float* p) { return *p; }
+  __device__ __forceinline__ static float dec(float x, float, float) { return x; }
+  __device__ __forceinline__ static void st(float* p, float v, float, float) { *p = v; }
 };
 template <> struct Codec<__half> {
-  __device__ __forceinline__ static float load(const __half* p, float w, float c) {
-    return fmaf(__half2float(__ldg(p)), w, w * c);
-  }
-  __device__ __forceinline__ static float loadc(const __half* p, float w, float c) {
-    return fmaf(__half2float(*p), w, w * c);
-  }
-  __device__ __forceinline__ static void store(__half* p, float v, float w, float c) {
-    *p = __float2half_rn((v - w * c) / w);
+  __device__ __forceinline__ static __half ld(const __half* p) { return __ldg(p); }
+  __device__ __forceinline__ static __half ldc(const __half* p) { return *p; }
+  __device__ __forceinline__ static float dec(__half x, float s, float off) { return fmaf(__half2float(x), s, off); }
+  __device__ __forceinline__ static void st(__half* p, float v, float inv_s, float off) {
+    *p = __float2half_rn((v - off) * inv_s);
   }
 };
 template <> struct Codec<__nv_bfloat16> {
-  __device__ __forceinline__ static float load(const __nv_bfloat16* p, float w, float c) {
-    return fmaf(__bfloat162float(__ldg(p)), w, w * c);
+  __device__ __forceinline__ static __nv_bfloat16 ld(const __nv_bfloat16* p) { return __ldg(p); }
+  __device__ __forceinline__ static __nv_bfloat16 ldc(const __nv_bfloat16* p) { return *p; }
+  __device__ __forceinline__ static float dec(__nv_bfloat16 x, float s, float off) {
+    return fmaf(__bfloat162float(x), s, off);
   }
-  __device__ __forceinline__ static float loadc(const __nv_bfloat16* p, float w, float c) {
-    return fmaf(__bfloat162float(*p), w, w * c);
-  }
-  __device__ __forceinline__ static void store(__nv_bfloat16* p, float v, float w, float c) {
-    *p = __float2bfloat16_rn((v - w * c) / w);
+  __device__ __forceinline__ static void st(__nv_bfloat16* p, float v, float inv_s, float off) {
+    *p = __float2bfloat16_rn((v - off) * inv_s);
   }
 };
 
-// Normaliser of slot a for the 16-bit codec (the weight, or 1 where it is 0).
-template <typename L>
-__host__ __device__ constexpr float norm_w(int a) {
-  return L::w(a) > 0.0f ? L::w(a) : 1.0f;
+// Population slot q of lattice L at p, rest-state constant c.
+template <typename T, typename L>
+__device__ __forceinline__ float pop_load(const T* p, int q, float c) {  // read-only data
+  return Codec<T>::dec(Codec<T>::ld(p), pow2_scale<L>(q), wprime<L>(q) * c);
+}
+template <typename T, typename L>
+__device__ __forceinline__ float pop_loadc(const T* p, int q, float c) { // data written in this kernel
+  return Codec<T>::dec(Codec<T>::ldc(p), pow2_scale<L>(q), wprime<L>(q) * c);
+}
+template <typename T, typename L>
+__device__ __forceinline__ void pop_store(T* p, int q, float v, float c) {
+  Codec<T>::st(p, v, 1.0f / pow2_scale<L>(q), wprime<L>(q) * c);
 }
 
 // ---------------------------------------------------------------------------

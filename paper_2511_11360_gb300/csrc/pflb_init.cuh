@@ -36,7 +36,8 @@ __global__ void init_kernel(const InitArgs args) {
     float mu = 0.0f;
     if constexpr (FAM == FAM_LIANG) {
       // Chemical potential of phi0, Eq. (chemical_potential), Sec. III stencil.
-      float lap = 0.0f;
+      float nb[QS];
+      nb[0] = phi;
 #pragma unroll
       for (int q = 1; q < QS; ++q) {
         int xn = x + LS::ex(q), yn = y + LS::ey(q), zn = z + LS::ez(q);
@@ -44,9 +45,9 @@ __global__ void init_kernel(const InitArgs args) {
         if (P.walls) yn = yn < 0 ? -1 - yn : (yn >= ny ? 2 * ny - 1 - yn : yn);
         else yn = yn < 0 ? yn + ny : (yn >= ny ? yn - ny : yn);
         zn = zn < 0 ? zn + nz : (zn >= nz ? zn - nz : zn);
-        lap += LS::w(q) * (args.phi0[xn + (long long)nx * (yn + (long long)ny * zn)] - phi);
+        nb[q] = args.phi0[xn + (long long)nx * (yn + (long long)ny * zn)];
       }
-      mu = P.beta4 * (phi - P.phiH) * (phi - P.phiL) * (phi - P.phi0) - P.kappa * 6.0f * lap;
+      mu = P.beta4 * (phi - P.phiH) * (phi - P.phiL) * (phi - P.phi0) - P.kappa * Sym<LS>::lap(nb, phi);
     }
 
 #pragma unroll
@@ -59,7 +60,7 @@ __global__ void init_kernel(const InitArgs args) {
       if constexpr (FAM == FAM_FAKHARI) geq = w * phi * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * usq);
       else if constexpr (FAM == FAM_LIANG) geq = (q == 0) ? phi + (w - 1.0f) * P.eta * mu : w * (P.eta * mu + 3.0f * phi * eu);
       else geq = w * phi * (1.0f + 3.0f * eu);
-      Codec<T>::store(g + (long long)q * N + idx, geq, norm_w<LG>(q), P.gref);
+      pop_store<T, LG>(g + (long long)q * N + idx, q, geq, P.gref);
     }
 #pragma unroll
     for (int q = 0; q < QF; ++q) {
@@ -72,7 +73,7 @@ __global__ void init_kernel(const InitArgs args) {
         feq = (q == 0) ? rho * w * (-1.5f * usq) : rho * w * (3.0f * eu + 4.5f * eu * eu - 1.5f * usq);
       else
         feq = w * (3.0f * eu + 4.5f * eu * eu - 1.5f * usq);
-      Codec<T>::store(f + (long long)q * N + idx, feq, norm_w<LF>(q), 0.0f);
+      pop_store<T, LF>(f + (long long)q * N + idx, q, feq, 0.0f);
     }
     if constexpr (FAM == FAM_LIANG) {
 #pragma unroll

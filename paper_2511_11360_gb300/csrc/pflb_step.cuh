@@ -16,6 +16,7 @@
 #pragma once
 
 #include "pflb_args.h"
+#include "pflb_symsum.cuh"
 
 namespace pflb {
 
@@ -71,6 +72,14 @@ __device__ __forceinline__ float finish_phi(const DevParams& P, float ps, float 
   else return ps;
 }
 
+// phi* = sum_a g_a (mirror-exact; the D3Q7 rest slot of the Allen-Cahn
+// families is identically zero and left out).
+template <typename LG, bool NO_REST, typename V>
+__device__ __forceinline__ float phi_star(const V& g) {
+  if constexpr (NO_REST) return Sym<LG>::moving(g);
+  else return g[0] + Sym<LG>::moving(g);
+}
+
 // ---------------------------------------------------------------------------
 // Collision of one cell. Inputs: pre-collision g, f; phi, phi*, grad phi,
 // lap phi (and for Cahn-Hilliard mu, lap mu, phi*u of the previous step).
@@ -93,16 +102,10 @@ struct Cell {
     const float fw = 1.0f - 0.5f * itau;
     const float inv_rho = 1.0f / rho;
     float grho[DIM], Fs[DIM], Fb[DIM], mom[DIM];
-    float sumf = 0.0f;
+    const float sum_nz = Sym<LF>::moving(f);
+    const float sumf = f[0] + sum_nz;
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) mom[k] = 0.0f;
-#pragma unroll
-    for (int q = 0; q < QF; ++q) {
-      sumf += f[q];
-#pragma unroll
-      for (int k = 0; k < DIM; ++k)
-        if (ecomp<LF>(q, k) != 0) mom[k] += (float)ecomp<LF>(q, k) * f[q];
-    }
+    for (int k = 0; k < DIM; ++k) mom[k] = Sym<LF>::first(f, k);
     const float mu = (FAM == FAM_LIANG) ? mu_in
         : P.beta4 * (phi - P.phiH) * (phi - P.phiL) * (phi - P.phi0) - P.kappa * lp;
 #pragma unroll
@@ -132,15 +135,7 @@ struct Cell {
 #pragma unroll
         for (int i = 0; i < DIM; ++i)
 #pragma unroll
-          for (int j = 0; j < DIM; ++j) Pi[i][j] = 0.0f;
-#pragma unroll
-        for (int q = 0; q < QF; ++q)
-#pragma unroll
-          for (int i = 0; i < DIM; ++i)
-#pragma unroll
-            for (int j = i; j < DIM; ++j)
-              if (ecomp<LF>(q, i) * ecomp<LF>(q, j) != 0)
-                Pi[i][j] += (float)(ecomp<LF>(q, i) * ecomp<LF>(q, j)) * f[q];
+          for (int j = i; j < DIM; ++j) Pi[i][j] = Sym<LF>::second(f, i, j);
         const float c = -3.0f * nu * itau;
 #pragma unroll
         for (int i = 0; i < DIM; ++i) {
@@ -173,6 +168,12 @@ struct Cell {
     for (int k = 0; k < DIM; ++k) usq += u[k] * u[k];
 
     // ---------------- phase field ----------------
+    // Equilibria whose zeroth moment is phi carry it exactly: where the rest
+    // population is stored it is phi minus the moving ones; weights multiply
+    // as hi + lo pairs (wmul), so no moment carries the bias of the FP32
+    // weights.
+    constexpr bool REST = (LG::w(0) > 0.0f) || (FAM == FAM_LIANG);
+    float geq[QG], G[QG];
     if constexpr (FAM == FAM_LIANG) {
       // Eq. (liang2_geq) and Eq. (liang2_G) with the backward-Euler d_t(phi u).
       const float emu = P.eta * mu;
@@ -183,8 +184,10 @@ struct Cell {
         dpu[k] = pu[k] - phiu[k];
         phiu[k] = pu[k];
       }
+      geq[0] = 0.0f;
+      G[0] = 0.0f;
 #pragma unroll
-      for (int q = 0; q < QG; ++q) {
+      for (int q = 1; q < QG; ++q) {
         float epu = 0.0f, edpu = 0.0f;
 #pragma unroll
         for (int k = 0; k < DIM; ++k)
@@ -192,11 +195,10 @@ struct Cell {
             epu += (float)ecomp<LG>(q, k) * pu[k];
             edpu += (float)ecomp<LG>(q, k) * dpu[k];
           }
-        const float w = LG::w(q);
-        const float geq = (q == 0) ? phi + (w - 1.0f) * emu : w * (emu + 3.0f * epu);
-        const float G = 3.0f * w * edpu;
-        g[q] = g[q] - (g[q] - geq) * P.inv_tau_phi + P.src_w_phi * G;
+        geq[q] = wmul<LG>(q, emu + 3.0f * epu);
+        G[q] = wmul<LG>(q, 3.0f * edpu);
       }
+      geq[0] = phi - Sym<LG>::moving(geq);   // = phi + (w_0 - 1) eta mu
     } else {
       float flux[DIM];
       bool has_cons = (FAM == FAM_FAKHARI || FAM == FAM_HU);
@@ -205,17 +207,19 @@ struct Cell {
         float g2 = 0.0f;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) g2 += gp[k] * gp[k];
-        const float s = (g2 >= P.eps2) ? P.counter_k * (P.phiH - phi) * (phi - P.phiL) * rsqrtf(g2) : 0.0f;
+        const float sc = (g2 >= P.eps2) ? P.counter_k * (P.phiH - phi) * (phi - P.phiL) * rsqrtf(g2) : 0.0f;
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) flux[k] = s * gp[k];
+        for (int k = 0; k < DIM; ++k) flux[k] = sc * gp[k];
       }
       float Rw = 0.0f, lam = 1.0f;
       if constexpr (FAM == FAM_CHAI || FAM == FAM_HU) {
         Rw = nonlocal_R<FAM>(P, phis, gamma);
         if constexpr (FAM == FAM_HU) { lam = P.lambda; Rw *= (1.0f - lam); }
       }
+      geq[0] = 0.0f;
+      G[0] = 0.0f;
 #pragma unroll
-      for (int q = 0; q < QG; ++q) {
+      for (int q = 1; q < QG; ++q) {
         float eu = 0.0f, ef = 0.0f;
 #pragma unroll
         for (int k = 0; k < DIM; ++k)
@@ -223,29 +227,35 @@ struct Cell {
             eu += (float)ecomp<LG>(q, k) * u[k];
             if (has_cons) ef += (float)ecomp<LG>(q, k) * flux[k];
           }
-        const float w = LG::w(q);
-        float geq;
         if constexpr (FAM == FAM_FAKHARI)
-          geq = w * phi * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * usq);  // Eq. (fakhari_geq)
+          geq[q] = wmul<LG>(q, phi * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * usq));  // Eq. (fakhari_geq)
         else
-          geq = w * phi * (1.0f + 3.0f * eu);                               // Eq. (Chai_geq)
-        float G;
-        if constexpr (FAM == FAM_FAKHARI) G = w * ef;
-        else if constexpr (FAM == FAM_CHAI) G = w * Rw;
-        else G = w * (lam * ef + Rw);                                       // Eq. (Hu_G)
-        g[q] = g[q] - (g[q] - geq) * P.inv_tau_phi + P.src_w_phi * G;
+          geq[q] = wmul<LG>(q, phi * (1.0f + 3.0f * eu));                               // Eq. (Chai_geq)
+        if constexpr (FAM == FAM_FAKHARI) G[q] = wmul<LG>(q, ef);
+        else if constexpr (FAM == FAM_CHAI) G[q] = wmul<LG>(q, Rw);
+        else G[q] = wmul<LG>(q, lam * ef + Rw);                                        // Eq. (Hu_G)
+      }
+      if constexpr (REST) {
+        geq[0] = phi - Sym<LG>::moving(geq);
+        if constexpr (FAM == FAM_CHAI || FAM == FAM_HU) G[0] = wmul<LG>(0, Rw);
       }
     }
+#pragma unroll
+    for (int q = 0; q < QG; ++q) g[q] = g[q] - (g[q] - geq[q]) * P.inv_tau_phi + P.src_w_phi * G[q];
 
     // ---------------- hydrodynamics ----------------
     if constexpr (FAM == FAM_LIANG) {
       // p by Eq. (liang_p_update); pressure-based f_eq and forcing of Eqs.
       // (liang2_feq), (liang2_F), (Gamma_beta).
-      const float w0 = LF::w(0);
       float udg = 0.0f;
 #pragma unroll
       for (int k = 0; k < DIM; ++k) udg += u[k] * grho[k];
-      p = cs2 / (1.0f - w0) * (sumf - f[0] + 0.5f * udg - rho * w0 * 1.5f * usq);
+      // 3p = X / (1 - w_0) with 1 - w_0 = 5/9 (D2Q9) or 2/3 (D3Q19), formed
+      // without a biased FP32 constant so the p -> f_eq -> p round trip is
+      // unbiased.
+      const float Xp = sum_nz + 0.5f * udg - wmul<LF>(0, rho * 1.5f * usq);
+      const float p3 = (DIM == 2) ? (Xp * 9.0f) / 5.0f : Xp * 1.5f;
+      p = p3 / 3.0f;
       float uF = 0.0f, ua = 0.0f;
 #pragma unroll
       for (int k = 0; k < DIM; ++k) {
@@ -263,11 +273,10 @@ struct Cell {
             eF += e * F[k];
             ea += e * cs2 * grho[k];
           }
-        const float w = LF::w(q);
-        const float Gam = w * (3.0f * eu + 4.5f * eu * eu - 1.5f * usq);
-        const float feq = (q == 0) ? 3.0f * p * (w - 1.0f) + rho * w * (-1.5f * usq)
-                                   : 3.0f * p * w + rho * Gam;
-        const float Fq = 3.0f * ((ea - ua) * Gam + (eF - uF) * (w + Gam));
+        const float Gam = wmul<LF>(q, 3.0f * eu + 4.5f * eu * eu - 1.5f * usq);
+        const float feq = (q == 0) ? wmul<LF>(q, p3) - p3 + wmul<LF>(q, rho * (-1.5f * usq))
+                                   : wmul<LF>(q, p3) + rho * Gam;
+        const float Fq = 3.0f * ((ea - ua) * Gam + (eF - uF) * Gam + wmul<LF>(q, eF - uF));
         f[q] = f[q] - (f[q] - feq) * itau + fw * Fq;
       }
     } else {
@@ -287,11 +296,10 @@ struct Cell {
             eu += e * u[k];
             eF += e * Ft[k];
           }
-        const float w = LF::w(q);
-        const float feq = w * (sumf + 3.0f * eu + 4.5f * eu * eu - 1.5f * usq);  // Eq. (fakhari_feq)
+        const float feq = wmul<LF>(q, sumf + 3.0f * eu + 4.5f * eu * eu - 1.5f * usq);  // Eq. (fakhari_feq)
         float Fq;
-        if constexpr (FAM == FAM_FAKHARI) Fq = 3.0f * w * eF;                     // Eq. (fakhari_F)
-        else Fq = w * (3.0f * eF + 9.0f * (eu * eF - cs2 * uFt));                 // Eq. (chai_F), Reading R2
+        if constexpr (FAM == FAM_FAKHARI) Fq = wmul<LF>(q, 3.0f * eF);                     // Eq. (fakhari_F)
+        else Fq = wmul<LF>(q, 3.0f * eF + 9.0f * eu * eF - 3.0f * uFt);                   // Eq. (chai_F), Reading R2
         f[q] = f[q] - (f[q] - feq) * itau + fw * Fq;
       }
     }
@@ -313,7 +321,7 @@ step_kernel(const StepArgs args) {
   constexpr int H = CH ? 2 : 1;                 // phi halo
   constexpr int HB = (DIM == 3) ? H : 0;
   constexpr int RA = TA + 2 * H, RB = TB + 2 * HB, PLANE = RA * RB;
-  constexpr int NSLOT = 2 * H + 2;
+  constexpr int NSLOT = CH ? 8 : 4;             // power of two >= 2H + 2
   constexpr int NHALO = PLANE - NT;
   constexpr int KH = (NHALO + NT - 1) / NT;
   constexpr int MHB = (DIM == 3) ? 1 : 0;       // mu region halo (CH)
@@ -328,8 +336,10 @@ step_kernel(const StepArgs args) {
 
   const DevParams& P = args.p;
   const int NA = P.nx, NB = (DIM == 3) ? P.ny : 1, NC = (DIM == 3) ? P.nz : P.ny;
-  const long long N = args.N;
-  const long long NAB = (long long)NA * NB;
+  // Element offsets into one population array, q*N + cell, fit in 32 bits
+  // (the host rejects Q*N >= 2^32).
+  const unsigned N = (unsigned)args.N;
+  const int NAB = NA * NB;
   const int tiles_a = (NA + TA - 1) / TA, tiles_b = (NB + TB - 1) / TB;
   int bid = blockIdx.x;
   const int ti = bid % tiles_a;
@@ -395,21 +405,21 @@ step_kernel(const StepArgs args) {
     return wrap_mod(c, NC);
   };
 
-  auto load_g = [&](long long idx, float (&gv)[QG]) -> float {
-    float s = 0.0f;
+  auto load_g = [&](unsigned idx, float (&gv)[QG]) -> float {
 #pragma unroll
     for (int q = 0; q < QG; ++q) {
       if (DIM == 3 && !CH && q == 0) { gv[q] = 0.0f; continue; }  // D3Q7 rest slot: w_0 = 0, g_0 = 0
-      gv[q] = Codec<T>::load(gsrc + (long long)q * N + idx, norm_w<LG>(q), P.gref);
-      s += gv[q];
+      gv[q] = pop_load<T, LG>(gsrc + (q * N + idx), q, P.gref);
     }
-    return s;
+    return phi_star<LG, (DIM == 3 && !CH)>(gv);
   };
+
+  auto ring = [&](int c) -> float* { return s_phi + (c & (NSLOT - 1)) * PLANE; };
 
   // Compute phi of logical plane c into ring slot; keep the own cell's g.
   auto produce = [&](int c, float (&gown)[QG]) {
-    const long long pofs = NAB * map_c(c);
-    float* slot = s_phi + ((c % NSLOT + NSLOT) % NSLOT) * PLANE;
+    const unsigned pofs = (unsigned)(NAB * map_c(c));
+    float* slot = ring(c);
     const float ps = load_g(own_ab + pofs, gown);
     slot[own_slot] = finish_phi<FAM>(P, ps, gamma);
 #pragma unroll
@@ -422,21 +432,26 @@ step_kernel(const StepArgs args) {
     }
   };
 
-  auto phi_at = [&](int c, int ra, int rb) -> float {
-    return s_phi[((c % NSLOT + NSLOT) % NSLOT) * PLANE + rb * RA + ra];
+  // Value at stencil offset q around ring position pos, with the three
+  // plane pointers of c-1, c, c+1 (compile-time offsets after unrolling).
+  auto ring_nb = [&](const float* pm, const float* p0, const float* pp, int pos, int q) -> float {
+    const int dc = dc_of<DIM, LS>(q);
+    const float* pl = dc < 0 ? pm : (dc > 0 ? pp : p0);
+    return pl[pos + db_of<DIM, LS>(q) * RA + da_of<DIM, LS>(q)];
   };
 
   // Cahn-Hilliard: mu of logical plane c over the tile + 1 region.
   auto make_mu = [&](int c) {
-    float* mslot = s_mu + ((c % MSLOT + MSLOT) % MSLOT) * MPLANE;
+    float* mslot = s_mu + (c & (MSLOT - 1)) * MPLANE;
+    const float *pm = ring(c - 1), *p0 = ring(c), *pp = ring(c + 1);
     auto one = [&](int ma, int mb) {
-      const int ra = ma + H - 1, rb = mb + HB - MHB;
-      const float pc = phi_at(c, ra, rb);
-      float lap = 0.0f;
+      const int pos = (mb + HB - MHB) * RA + (ma + H - 1);
+      const float pc = p0[pos];
+      float nb[QS];
+      nb[0] = pc;
 #pragma unroll
-      for (int q = 1; q < QS; ++q)
-        lap += LS::w(q) * (phi_at(c + dc_of<DIM, LS>(q), ra + da_of<DIM, LS>(q), rb + db_of<DIM, LS>(q)) - pc);
-      lap *= 6.0f;
+      for (int q = 1; q < QS; ++q) nb[q] = ring_nb(pm, p0, pp, pos, q);
+      const float lap = Sym<LS>::lap(nb, pc);
       mslot[mb * MRA + ma] = P.beta4 * (pc - P.phiH) * (pc - P.phiL) * (pc - P.phi0) - P.kappa * lap;
     };
     one(tx + 1, ty + MHB);
@@ -482,8 +497,9 @@ step_kernel(const StepArgs args) {
   const int aw = (a < NA) ? a : 0, bw = (b < NB) ? b : 0;
   const int am = aw == 0 ? NA - 1 : aw - 1, ap = aw == NA - 1 ? 0 : aw + 1;
   const int bm = bw == 0 ? NB - 1 : bw - 1, bp = bw == NB - 1 ? 0 : bw + 1;
+  const int rbm = bm * NA, rbw = bw * NA, rbp = bp * NA;
   auto A_of = [&](int d) { return d < 0 ? am : (d > 0 ? ap : aw); };
-  auto B_of = [&](int d) { return d < 0 ? bm : (d > 0 ? bp : bw); };
+  auto RB_of = [&](int d) { return d < 0 ? rbm : (d > 0 ? rbp : rbw); };
 
   for (int c = c0; c < c1; ++c) {
     if constexpr (CH) {
@@ -497,44 +513,48 @@ step_kernel(const StepArgs args) {
     }
 
     if (active) {
-      // Stencils of Sec. III on the ring (stencil lattice weights).
-      const int ra = tx + H, rb = ty + HB;
-      const float pc = phi_at(c, ra, rb);
-      float gp[DIM], lp = 0.0f;
+      // Stencils of Sec. III on the ring (stencil lattice weights). Both are
+      // formed from differences phi(x + e) - phi(x) (the gradient's sum of
+      // w e phi(x) vanishes), which are exact in FP32 for nearby values.
+      const float *pm = ring(c - 1), *p0 = ring(c), *pp = ring(c + 1);
+      const float pc = p0[own_slot];
+      float gp[DIM], lp;
+      {
+        float nb[QS];
+        nb[0] = pc;
 #pragma unroll
-      for (int k = 0; k < DIM; ++k) gp[k] = 0.0f;
+        for (int q = 1; q < QS; ++q) nb[q] = ring_nb(pm, p0, pp, own_slot, q);
+        lp = Sym<LS>::lap(nb, pc);
 #pragma unroll
-      for (int q = 1; q < QS; ++q) {
-        const float v = phi_at(c + dc_of<DIM, LS>(q), ra + da_of<DIM, LS>(q), rb + db_of<DIM, LS>(q));
-        lp += LS::w(q) * (v - pc);
-#pragma unroll
-        for (int k = 0; k < DIM; ++k)
-          if (ecomp<LS>(q, k) != 0) gp[k] += LS::w(q) * (float)ecomp<LS>(q, k) * v;
+        for (int k = 0; k < DIM; ++k) gp[k] = Sym<LS>::grad(nb, k);
       }
-      lp *= 6.0f;
-#pragma unroll
-      for (int k = 0; k < DIM; ++k) gp[k] *= 3.0f;
 
       float mu_c = 0.0f, lmu = 0.0f;
       if constexpr (CH) {
-        auto mu_at = [&](int cc, int ma, int mb) {
-          return s_mu[((cc % MSLOT + MSLOT) % MSLOT) * MPLANE + mb * MRA + ma];
-        };
-        const int ma = tx + 1, mb = ty + MHB;
-        mu_c = mu_at(c, ma, mb);
+        const float* mm = s_mu + ((c - 1) & (MSLOT - 1)) * MPLANE;
+        const float* m0 = s_mu + (c & (MSLOT - 1)) * MPLANE;
+        const float* mp = s_mu + ((c + 1) & (MSLOT - 1)) * MPLANE;
+        const int mpos = (ty + MHB) * MRA + (tx + 1);
+        mu_c = m0[mpos];
+        float nb[QS];
+        nb[0] = mu_c;
 #pragma unroll
-        for (int q = 1; q < QS; ++q)
-          lmu += LS::w(q) * (mu_at(c + dc_of<DIM, LS>(q), ma + da_of<DIM, LS>(q), mb + db_of<DIM, LS>(q)) - mu_c);
-        lmu *= 6.0f;
+        for (int q = 1; q < QS; ++q) {
+          const int dc = dc_of<DIM, LS>(q);
+          const float* ml = dc < 0 ? mm : (dc > 0 ? mp : m0);
+          nb[q] = ml[mpos + db_of<DIM, LS>(q) * MRA + da_of<DIM, LS>(q)];
+        }
+        lmu = Sym<LS>::lap(nb, mu_c);
       }
 
       const int cm = (c == 0) ? NC - 1 : c - 1, cp = (c == NC - 1) ? 0 : c + 1;
       const bool lo_wall = walls && c == 0, hi_wall = walls && c == NC - 1;
-      auto C_of = [&](int d) { return d < 0 ? cm : (d > 0 ? cp : c); };
+      const int pcm = cm * NAB, pc0 = c * NAB, pcp = cp * NAB;
+      auto PC_of = [&](int d) { return d < 0 ? pcm : (d > 0 ? pcp : pc0); };
       auto crosses = [&](int dcv) { return (dcv < 0 && lo_wall) || (dcv > 0 && hi_wall); };
-      const long long idx = (long long)aw + NA * ((long long)bw + (long long)NB * c);
-      auto nidx = [&](int da, int db, int dc) -> long long {
-        return (long long)A_of(da) + NA * ((long long)B_of(db) + (long long)NB * C_of(dc));
+      const unsigned idx = (unsigned)(aw + rbw + pc0);
+      auto nidx = [&](int da, int db, int dc) -> unsigned {
+        return (unsigned)(A_of(da) + RB_of(db) + PC_of(dc));
       };
 
       // Pre-collision f (AA pattern).
@@ -542,23 +562,18 @@ step_kernel(const StepArgs args) {
 #pragma unroll
       for (int q = 0; q < QF; ++q) {
         const int da = da_of<DIM, LF>(q), db = db_of<DIM, LF>(q), dc = dc_of<DIM, LF>(q);
-        const float wn = norm_w<LF>(q);
-        if (args.parity == 0) {
-          f[q] = Codec<T>::loadc(fb + (long long)q * N + idx, wn, 0.0f);
-        } else if (crosses(-dc)) {
-          f[q] = Codec<T>::loadc(fb + (long long)q * N + idx, wn, 0.0f);
+        if (args.parity == 0 || crosses(-dc)) {
+          f[q] = pop_loadc<T, LF>(fb + (q * N + idx), q, 0.0f);
         } else {
-          f[q] = Codec<T>::loadc(fb + (long long)LF::opp(q) * N + nidx(-da, -db, -dc), norm_w<LF>(LF::opp(q)), 0.0f);
+          f[q] = pop_loadc<T, LF>(fb + (LF::opp(q) * N + nidx(-da, -db, -dc)), q, 0.0f);
         }
       }
       float phiu[DIM];
       if constexpr (CH) {
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) phiu[k] = args.phiu[(long long)k * N + idx];
+        for (int k = 0; k < DIM; ++k) phiu[k] = args.phiu[k * N + idx];
       }
-      float phis = 0.0f;
-#pragma unroll
-      for (int q = 0; q < QG; ++q) phis += g0[q];
+      const float phis = phi_star<LG, (DIM == 3 && !CH)>(g0);
 
       float u[DIM], rho, p;
       float gnew[QG];
@@ -587,12 +602,12 @@ step_kernel(const StepArgs args) {
       if (args.macro) {
         args.out_phi[idx] = pc;
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) args.out_u[(long long)k * N + idx] = u[k];
+        for (int k = 0; k < DIM; ++k) args.out_u[k * N + idx] = u[k];
         args.out_p[idx] = p;
       } else {
         if constexpr (CH) {
 #pragma unroll
-          for (int k = 0; k < DIM; ++k) args.phiu[(long long)k * N + idx] = phiu[k];
+          for (int k = 0; k < DIM; ++k) args.phiu[k * N + idx] = phiu[k];
         }
         // g: two-array push, bounce-back into the own cell at walls.
         const float uw_lo = P.moving ? P.wall_u[0] : 0.0f, uw_hi = P.moving ? P.wall_u[1] : 0.0f;
@@ -600,15 +615,14 @@ step_kernel(const StepArgs args) {
         for (int q = 0; q < QG; ++q) {
           if (DIM == 3 && !CH && q == 0) continue;
           const int da = da_of<DIM, LG>(q), db = db_of<DIM, LG>(q), dc = dc_of<DIM, LG>(q);
-          const float wn = norm_w<LG>(q);
           if (P.freeze) {
-            Codec<T>::store(gdst + (long long)q * N + idx, g0[q], wn, P.gref);
+            pop_store<T, LG>(gdst + (q * N + idx), q, g0[q], P.gref);
           } else if (crosses(dc)) {
             const float uw = dc < 0 ? uw_lo : uw_hi;
             const float v = gnew[q] - 6.0f * LG::w(q) * pc * (float)LG::ex(q) * uw;
-            Codec<T>::store(gdst + (long long)LG::opp(q) * N + idx, v, norm_w<LG>(LG::opp(q)), P.gref);
+            pop_store<T, LG>(gdst + (LG::opp(q) * N + idx), q, v, P.gref);
           } else {
-            Codec<T>::store(gdst + (long long)q * N + nidx(da, db, dc), gnew[q], wn, P.gref);
+            pop_store<T, LG>(gdst + (q * N + nidx(da, db, dc)), q, gnew[q], P.gref);
           }
         }
         // f: AA pattern.
@@ -623,9 +637,9 @@ step_kernel(const StepArgs args) {
             v -= 6.0f * LF::w(q) * sc * (float)LF::ex(q) * uw;
           }
           if (args.parity == 0 || cr) {
-            Codec<T>::store(fb + (long long)LF::opp(q) * N + idx, v, norm_w<LF>(LF::opp(q)), 0.0f);
+            pop_store<T, LF>(fb + (LF::opp(q) * N + idx), q, v, 0.0f);
           } else {
-            Codec<T>::store(fb + (long long)q * N + nidx(da, db, dc), v, norm_w<LF>(q), 0.0f);
+            pop_store<T, LF>(fb + (q * N + nidx(da, db, dc)), q, v, 0.0f);
           }
         }
       }
