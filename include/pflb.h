@@ -95,9 +95,9 @@ typedef struct pflb_params {
   double force_density[3]; /* uniform force density added to F_b */
   double lundgren_A;    /* linear forcing F = A rho u (turbulence driver) */
   double wall_u[2];     /* x velocity of the bottom and top wall (bc_y = 2) */
-  double grad_eps;      /* |grad phi| below which the interface normal, and the
-                           conservative counter flux, are 0 (1e-6: the FP32
-                           noise floor of a gradient of phi = O(1)) */
+  double grad_eps;      /* regularisation of the interface normal,
+                           n = grad phi / sqrt(|grad phi|^2 + grad_eps^2)
+                           (1e-4; the paper leaves n undefined at 0) */
 } pflb_params;
 
 /* Bookkeeping of one state: sums over all cells of its macroscopic fields. */

@@ -108,7 +108,7 @@ def default_params(**kw):
              lambda_hybrid=0.9,      # Sec. III: lambda = 0.9 for Hu2019
              eta_ch=1.0,             # Reading R12
              gravity=(0.0, 0.0, 0.0), force_density=(0.0, 0.0, 0.0),
-             lundgren_A=0.0, wall_u=(0.0, 0.0), grad_eps=1e-6,
+             lundgren_A=0.0, wall_u=(0.0, 0.0), grad_eps=1e-4,
              freeze_phi=0)
     p.update(kw)
     return p
@@ -306,15 +306,17 @@ def feq_pressure(lat, p, rho, u):
 def source_conservative(P, lat, phi, grad_phi):
     """G = w e . [ sqrt(2 beta/kappa) (phi_H - phi)(phi - phi_L) grad(phi)/|grad(phi)| ]
     Eq. (fakhari_G_modified). Reading R6: the unit normal is undefined where
-    the gradient vanishes; it is taken as zero where |grad phi| < eps, with
-    eps = 1e-6 by default (below that a gradient of phi = O(1) is at the FP32
-    noise floor and its direction carries no information)."""
+    the gradient vanishes; it is regularised smoothly as
+    n = grad(phi) / sqrt(|grad phi|^2 + eps^2), eps = 1e-4 by default (three
+    orders below interface gradients ~ 1/xi). A hard cut-off, or a much
+    smaller eps, makes the flux jump or follow the direction of rounding-level
+    gradients inside droplets and in bulk over/undershoots, where
+    (phi_H - phi)(phi - phi_L) is not small."""
     c = derived(P)
     k = np.sqrt(2.0 * c["beta"] / c["kappa"])
     g2 = _udotu(grad_phi)
     eps = P["grad_eps"]
-    safe = np.where(g2 < eps * eps, 1.0, np.sqrt(np.where(g2 < eps * eps, 1.0, g2)))
-    n = np.where(g2 < eps * eps, 0.0, 1.0) * grad_phi / safe
+    n = grad_phi / np.sqrt(g2 + eps * eps)
     flux = k * (P["phi_H"] - phi) * (phi - P["phi_L"]) * n
     w = lat.w.reshape((-1,) + (1,) * phi.ndim)
     return w * _edot(lat, flux)

@@ -128,7 +128,7 @@ struct DevParams {
   float grav[3], fdens[3];
   float lundA;
   float wall_u[2];          // bottom, top
-  float eps2;               // grad_eps^2
+  float eps2;               // grad_eps^2 (normal regularisation)
   float gref;               // rest-state offset of g in 16-bit storage
 };
 

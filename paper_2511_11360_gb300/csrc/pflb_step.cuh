@@ -203,11 +203,12 @@ struct Cell {
       float flux[DIM];
       bool has_cons = (FAM == FAM_FAKHARI || FAM == FAM_HU);
       if (has_cons) {
-        // Conservative counter term, Eq. (fakhari_G_modified); Reading R6 guard.
+        // Conservative counter term, Eq. (fakhari_G_modified), with the
+        // normal regularised as grad phi / sqrt(|grad phi|^2 + eps^2) (R6).
         float g2 = 0.0f;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) g2 += gp[k] * gp[k];
-        const float sc = (g2 >= P.eps2) ? P.counter_k * (P.phiH - phi) * (phi - P.phiL) * rsqrtf(g2) : 0.0f;
+        const float sc = P.counter_k * (P.phiH - phi) * (phi - P.phiL) * rsqrtf(g2 + P.eps2);
 #pragma unroll
         for (int k = 0; k < DIM; ++k) flux[k] = sc * gp[k];
       }

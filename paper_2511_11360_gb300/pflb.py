@@ -141,7 +141,7 @@ def make_params(d):
     for k in ("phi_H", "phi_L", "rho_H", "rho_L", "nu_H", "nu_L", "sigma", "W", "M",
               "lambda_hybrid", "eta_ch", "lundgren_A", "grad_eps"):
         setattr(p, k, float(d.get(k, {"phi_H": 1.0, "phi_L": 0.0, "lambda_hybrid": 0.9,
-                                        "eta_ch": 1.0, "grad_eps": 1e-6}.get(k, 0.0))))
+                                        "eta_ch": 1.0, "grad_eps": 1e-4}.get(k, 0.0))))
     g = d.get("gravity", (0.0, 0.0, 0.0))
     fd = d.get("force_density", (0.0, 0.0, 0.0))
     wu = d.get("wall_u", (0.0, 0.0))
@@ -259,3 +259,4 @@ def lattice(dim, which):
     if rc != PFLB_OK:
         raise PflbError(rc, "pflb_lattice")
     return e[: 3 * q.value].reshape(q.value, 3), w[: q.value]
+

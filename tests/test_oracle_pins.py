@@ -316,8 +316,11 @@ def test_step_commutes_with_reflection(fam, dim):
     st = O.run(P, O.init_state(P, phi, u), 2)
     a = _reflect_x(P, O.run(P, st, 3))
     b = O.run(P, _reflect_x(P, st), 3)
-    assert np.allclose(a.g, b.g, atol=1e-14, rtol=0)
-    assert np.allclose(a.f, b.f, atol=1e-14, rtol=0)
+    # FP64 sums in a different order differ by ~1e-17; the regularised normal
+    # (Lipschitz ~ k (1-phi) phi / eps ~ 1e3) lifts that to ~1e-13, while a
+    # wrong sign or index gives O(1e-3).
+    assert np.allclose(a.g, b.g, atol=1e-12, rtol=0)
+    assert np.allclose(a.f, b.f, atol=1e-12, rtol=0)
 
 
 @pytest.mark.parametrize("fam", C.FAMILIES, ids=lambda f: C.FAMILY_NAMES[f])
@@ -343,8 +346,8 @@ def test_step_commutes_with_axis_swap_3d(fam):
 
     a = swap(O.run(P, st, 2))
     b = O.run(P, swap(st), 2)
-    assert np.allclose(a.g, b.g, atol=1e-14, rtol=0)
-    assert np.allclose(a.f, b.f, atol=1e-14, rtol=0)
+    assert np.allclose(a.g, b.g, atol=1e-12, rtol=0)
+    assert np.allclose(a.f, b.f, atol=1e-12, rtol=0)
 
 
 @pytest.mark.parametrize("fam", C.FAMILIES, ids=lambda f: C.FAMILY_NAMES[f])
