@@ -189,6 +189,41 @@ int pflb_lattice(int32_t dim, int32_t which, int32_t* q, int32_t* e, double* w);
 int pflb_destroy(pflb_handle* h);
 const char* pflb_last_error(const pflb_handle* h);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free phase-field sums. (The paper has no counterpart: this is a
+ * service of the library for callers that cannot allocate device memory.)
+ *
+ * Some callers must not call cudaMalloc: an application that manages every
+ * byte of device memory through its own allocator and forbids allocations
+ * behind its back, or a latency-bound loop that cannot pay for the
+ * device-wide synchronisation that cudaMalloc and cudaFree imply. For them,
+ * pflb_phase_sums_static computes the phase-field part of pflb_observables --
+ * sum_phi, vol_smooth, vol_count, phi_max, phi_min and the centroid -- of a
+ * phi field the caller owns, without allocating anything: no cudaMalloc, no
+ * cudaFree, no allocating library call. Its scratch space is a file-scope
+ * device array of PFLB_STATIC_PARTIALS + 1 records (about 230 KB) that every
+ * GPU loading the library holds until the process exits.
+ *
+ *   params  only dim, nx, ny, nz, phi_H, phi_L are read;
+ *   phi     device pointer to N = nx*ny*nz floats (field layout as above);
+ *   out     host struct; ke is 0 and step is -1 (no velocity, no handle);
+ *   stream  cudaStream_t (may be NULL); the call synchronises it.
+ *
+ * Returns PFLB_EINVAL for a NULL argument, bad sizes, phi_H == phi_L, or
+ * N > PFLB_STATIC_MAX_CELLS (2^28 cells: the scratch holds one partial record
+ * per 65536 cells); PFLB_ECUDA without a device or on a CUDA error. The first
+ * call on a device looks up the scratch array's device address (with that
+ * device current); make that first call before any stream capture. The
+ * result does not depend on the previous call (every record used is written
+ * before it is read), but all calls share the array: calls that overlap on
+ * the GPU (different streams or host threads) race and must be serialised.
+ * ------------------------------------------------------------------------- */
+#define PFLB_STATIC_PARTIALS 4096
+#define PFLB_STATIC_CELLS_PER_BLOCK 65536LL
+#define PFLB_STATIC_MAX_CELLS (PFLB_STATIC_PARTIALS * PFLB_STATIC_CELLS_PER_BLOCK)
+int pflb_phase_sums_static(const pflb_params* params, const float* phi, pflb_obs* out,
+                           void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

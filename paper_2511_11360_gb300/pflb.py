@@ -78,6 +78,8 @@ SIGNATURES = {
     "pflb_lattice": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                     ctypes.c_void_p, ctypes.c_void_p]),
     "pflb_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "pflb_phase_sums_static": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_void_p, ctypes.POINTER(Obs),
+                                              ctypes.c_void_p]),
     "pflb_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
 }
 
@@ -260,3 +262,17 @@ def lattice(dim, which):
         raise PflbError(rc, "pflb_lattice")
     return e[: 3 * q.value].reshape(q.value, 3), w[: q.value]
 
+
+STATIC_MAX_CELLS = 4096 * 65536
+
+
+def phase_sums_static(params, phi, stream=None):
+    """pflb_phase_sums_static: the phase-field sums of a device phi field with
+    no device allocation (for callers that cannot allocate; see pflb.h)."""
+    lib = load_library()
+    p = make_params(params)
+    o = Obs()
+    rc = lib.pflb_phase_sums_static(ctypes.byref(p), _ptr(phi), ctypes.byref(o), _stream(stream))
+    if rc != PFLB_OK:
+        raise PflbError(rc, "pflb_phase_sums_static")
+    return o.to_dict()
