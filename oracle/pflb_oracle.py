@@ -22,6 +22,8 @@ Sec. II D 1).
 Parity pins: tests/test_oracle_pins.py and tests/test_oracle_physics.py.
 """
 
+import math
+
 import numpy as np
 
 __all__ = [
@@ -167,25 +169,25 @@ def _neighbour(padded, r, e, shape):
 def gradient(field, lat, walls=False):
     """grad(phi)(x) = 1/(c_s^2 dt) sum_a w_a e_a phi(x + e_a dt)   (Sec. III)."""
     Pd = _pad(field, 1, walls)
-    out = np.zeros((lat.d,) + field.shape)
+    out = np.zeros((lat.d,) + field.shape, dtype=field.dtype)
     for a in range(lat.Q):
         if not np.any(lat.e[a]):
             continue
         nb = _neighbour(Pd, 1, lat.e[a], field.shape)
         for k in range(lat.d):
             if lat.e[a, k]:
-                out[k] += lat.w[a] * lat.ef[a, k] * nb
+                out[k] += float(lat.w[a] * lat.ef[a, k]) * nb
     return out / lat.cs2
 
 
 def laplacian(field, lat, walls=False):
     """lap(phi)(x) = 2/(c_s^2 dt^2) sum_a w_a [phi(x + e_a dt) - phi(x)]   (Sec. III)."""
     Pd = _pad(field, 1, walls)
-    out = np.zeros(field.shape)
+    out = np.zeros(field.shape, dtype=field.dtype)
     for a in range(lat.Q):
         if not np.any(lat.e[a]):
             continue
-        out += lat.w[a] * (_neighbour(Pd, 1, lat.e[a], field.shape) - field)
+        out += float(lat.w[a]) * (_neighbour(Pd, 1, lat.e[a], field.shape) - field)
     return 2.0 * out / lat.cs2
 
 
@@ -248,7 +250,7 @@ def nonlocal_R(P, phi, gamma):
 # --------------------------------------------------------------------------
 def _edot(lat, v):
     """(e_a . v) for every velocity a: shape (Q, *field)."""
-    return np.tensordot(lat.ef, v, axes=([1], [0]))
+    return np.tensordot(lat.ef.astype(v.dtype), v, axes=([1], [0]))
 
 
 def _udotu(u):
@@ -259,14 +261,14 @@ def geq_fakhari(lat, phi, u):
     """g_eq = w phi [1 + e.u/c_s^2 + (e.u)^2/(2 c_s^4) - u.u/(2 c_s^2)]   Eq. (fakhari_geq)."""
     eu = _edot(lat, u)
     cs2 = lat.cs2
-    w = lat.w.reshape((-1,) + (1,) * phi.ndim)
+    w = lat.w.astype(phi.dtype).reshape((-1,) + (1,) * phi.ndim)
     return w * phi * (1.0 + eu / cs2 + eu ** 2 / (2 * cs2 ** 2) - _udotu(u) / (2 * cs2))
 
 
 def geq_chai(lat, phi, u):
     """g_eq = w phi (1 + e.u/c_s^2)      Eq. (Chai_geq); also Hu2019 (Sec. II C 4)."""
     eu = _edot(lat, u)
-    w = lat.w.reshape((-1,) + (1,) * phi.ndim)
+    w = lat.w.astype(phi.dtype).reshape((-1,) + (1,) * phi.ndim)
     return w * phi * (1.0 + eu / lat.cs2)
 
 
@@ -274,9 +276,9 @@ def geq_liang2014(lat, phi, u, mu, eta):
     """Eq. (liang2_geq): a = 0: phi + (w_0 - 1) eta mu;
     a != 0: w eta mu + w e.(phi u)/c_s^2."""
     eu = _edot(lat, phi * u)
-    w = lat.w.reshape((-1,) + (1,) * phi.ndim)
+    w = lat.w.astype(phi.dtype).reshape((-1,) + (1,) * phi.ndim)
     out = w * eta * mu + w * eu / lat.cs2
-    out[0] = phi + (lat.w[0] - 1.0) * eta * mu
+    out[0] = phi + float(lat.w[0] - 1.0) * eta * mu
     return out
 
 
@@ -287,7 +289,7 @@ def feq_velocity(lat, P_over_rho_cs2, u):
     to sum f (Reading R4)."""
     eu = _edot(lat, u)
     cs2 = lat.cs2
-    w = lat.w.reshape((-1,) + (1,) * (u.ndim - 1))
+    w = lat.w.astype(u.dtype).reshape((-1,) + (1,) * (u.ndim - 1))
     return w * P_over_rho_cs2 + w * (eu / cs2 + eu ** 2 / (2 * cs2 ** 2) - _udotu(u) / (2 * cs2))
 
 
@@ -297,9 +299,9 @@ def feq_pressure(lat, p, rho, u):
     with [...] = e.u/c_s^2 + (e.u)^2/(2c_s^4) - u.u/(2c_s^2)."""
     eu = _edot(lat, u)
     cs2 = lat.cs2
-    w = lat.w.reshape((-1,) + (1,) * (u.ndim - 1))
+    w = lat.w.astype(u.dtype).reshape((-1,) + (1,) * (u.ndim - 1))
     out = (p / cs2) * w + rho * w * (eu / cs2 + eu ** 2 / (2 * cs2 ** 2) - _udotu(u) / (2 * cs2))
-    out[0] = (p / cs2) * (lat.w[0] - 1.0) + rho * lat.w[0] * (-_udotu(u) / (2 * cs2))
+    out[0] = (p / cs2) * float(lat.w[0] - 1.0) + rho * float(lat.w[0]) * (-_udotu(u) / (2 * cs2))
     return out
 
 
@@ -313,18 +315,18 @@ def source_conservative(P, lat, phi, grad_phi):
     gradients inside droplets and in bulk over/undershoots, where
     (phi_H - phi)(phi - phi_L) is not small."""
     c = derived(P)
-    k = np.sqrt(2.0 * c["beta"] / c["kappa"])
+    k = math.sqrt(2.0 * c["beta"] / c["kappa"])
     g2 = _udotu(grad_phi)
     eps = P["grad_eps"]
     n = grad_phi / np.sqrt(g2 + eps * eps)
     flux = k * (P["phi_H"] - phi) * (phi - P["phi_L"]) * n
-    w = lat.w.reshape((-1,) + (1,) * phi.ndim)
+    w = lat.w.astype(phi.dtype).reshape((-1,) + (1,) * phi.ndim)
     return w * _edot(lat, flux)
 
 
 def force_fakhari(lat, F, rho):
     """F_b = w e.F/(rho c_s^2)      Eq. (fakhari_F)."""
-    w = lat.w.reshape((-1,) + (1,) * rho.ndim)
+    w = lat.w.astype(rho.dtype).reshape((-1,) + (1,) * rho.ndim)
     return w * _edot(lat, F) / (rho * lat.cs2)
 
 
@@ -339,7 +341,7 @@ def force_guo(lat, F, rho, u):
     eF = _edot(lat, Ft)
     uF = np.sum(u * Ft, axis=0)
     cs2 = lat.cs2
-    w = lat.w.reshape((-1,) + (1,) * rho.ndim)
+    w = lat.w.astype(rho.dtype).reshape((-1,) + (1,) * rho.ndim)
     return w * (eF / cs2 + (eu * eF - cs2 * uF) / cs2 ** 2)
 
 
@@ -349,7 +351,7 @@ def force_liang2014(lat, u, grad_rho, Ftot):
     Gamma_b = w (e.u/c_s^2 + (e.u)^2/(2c_s^4) - u.u/(2c_s^2)),  s_b = w + Gamma_b."""
     cs2 = lat.cs2
     eu = _edot(lat, u)
-    w = lat.w.reshape((-1,) + (1,) * (u.ndim - 1))
+    w = lat.w.astype(u.dtype).reshape((-1,) + (1,) * (u.ndim - 1))
     Gam = w * (eu / cs2 + eu ** 2 / (2 * cs2 ** 2) - _udotu(u) / (2 * cs2))
     s = w + Gam
     vec_a = cs2 * grad_rho            # grad(rho c_s^2), c_s^2 constant
@@ -382,7 +384,7 @@ def _shape(P):
 
 
 def _vec(P, key, like):
-    v = np.asarray(P[key], dtype=np.float64)[: P["dim"]]
+    v = np.asarray(P[key], dtype=like.dtype)[: P["dim"]]
     return v.reshape((-1,) + (1,) * like.ndim) * np.ones_like(like)
 
 
@@ -440,7 +442,7 @@ def macroscopic(P, st, gamma=None):
     Fs = mu * grad_phi                                         # F_s = mu_phi grad(phi)
     Fb = rho * _vec(P, "gravity", rho) + _vec(P, "force_density", rho)  # F_b = rho g (+ uniform density)
     A = P["lundgren_A"]
-    mom = np.tensordot(lf.ef.T, f, axes=([1], [0]))            # sum_b e_b f_b
+    mom = np.tensordot(lf.ef.T.astype(f.dtype), f, axes=([1], [0]))  # sum_b e_b f_b
 
     if fam == LIANG2014:
         # Eq. (liang2014_velocity_update); F_a = (rho_H-rho_L)/(phi_H-phi_L) div(M grad mu) u.
@@ -454,7 +456,7 @@ def macroscopic(P, st, gamma=None):
         FL = A * rho * u
         F = Fs + Fa + Fb + FL
         # Pressure, Eq. (liang_p_update) (Sec. II D 1: "the same manner as in Liang2018").
-        w0 = lf.w[0]
+        w0 = float(lf.w[0])
         p = lf.cs2 / (1.0 - w0) * (f[1:].sum(axis=0) + 0.5 * np.sum(u * grad_rho, axis=0)
                                    + rho * w0 * (-_udotu(u) / (2 * lf.cs2)))
         m.update(lap_mu=lap_mu, Fa=Fa, p=p, u=u, F=F, Fs=Fs, Fb=Fb + FL)
@@ -475,7 +477,7 @@ def macroscopic(P, st, gamma=None):
     Fmu = np.zeros_like(u1)
     for i in range(d):
         for j in range(d):
-            Pij = np.tensordot(lf.ef[:, i] * lf.ef[:, j], fneq, axes=([0], [0]))
+            Pij = np.tensordot((lf.ef[:, i] * lf.ef[:, j]).astype(fneq.dtype), fneq, axes=([0], [0]))
             Sij = -Pij / (tau * lf.cs2)
             Fmu[i] += nu * Sij * grad_rho[j]
     Fo = Fs + Fb + Fp + Fmu
@@ -503,11 +505,11 @@ def collide(P, st, m):
         G = source_conservative(P, lg, phi, m["grad_phi"])
     elif fam == CHAI2018:
         geq = geq_chai(lg, phi, u)
-        w = lg.w.reshape((-1,) + (1,) * phi.ndim)
+        w = lg.w.astype(phi.dtype).reshape((-1,) + (1,) * phi.ndim)
         G = w * m["R"]                                        # Eq. (chai_G)
     elif fam == HU2019:
         geq = geq_chai(lg, phi, u)
-        w = lg.w.reshape((-1,) + (1,) * phi.ndim)
+        w = lg.w.astype(phi.dtype).reshape((-1,) + (1,) * phi.ndim)
         lam = m["lam"]
         G = lam * source_conservative(P, lg, phi, m["grad_phi"]) + (1.0 - lam) * w * m["R"]  # Eq. (Hu_G)
     elif fam == LIANG2014:
@@ -515,7 +517,7 @@ def collide(P, st, m):
         phiu_new = phi * u
         # d_t(phi u) by backward Euler, Sec. III B: [phi u(t) - phi u(t - dt)]/dt.
         dtphiu = phiu_new - st.phiu_prev
-        w = lg.w.reshape((-1,) + (1,) * phi.ndim)
+        w = lg.w.astype(phi.dtype).reshape((-1,) + (1,) * phi.ndim)
         G = w * _edot(lg, dtphiu) / lg.cs2                    # Eq. (liang2_G)
     else:
         raise ValueError("family")
@@ -567,7 +569,7 @@ def stream(P, lat, post, wall_scale):
             sl = [slice(None)] * d
             sl[ay] = row
             sl = tuple(sl)
-            corr = 2.0 * lat.w[a] * lat.ef[a, 0] * uw / lat.cs2
+            corr = float(2.0 * lat.w[a] * lat.ef[a, 0] * uw / lat.cs2)
             out[a][sl] = post[b][sl] + corr * wall_scale[sl]
     return out
 
@@ -575,11 +577,13 @@ def stream(P, lat, post, wall_scale):
 # --------------------------------------------------------------------------
 # Initial state, step, run
 # --------------------------------------------------------------------------
-def init_state(P, phi0, u0):
-    """Populations at equilibrium with the given phi and u and p = 0 (Reading R8)."""
+def init_state(P, phi0, u0, dtype=np.float64):
+    """Populations at equilibrium with the given phi and u and p = 0 (Reading R8).
+    Every later step works in the dtype of the state (float64 unless asked
+    otherwise; float32 only serves to size the effect of FP32 rounding)."""
     lg, lf, ls = lattices_for(P["dim"])
-    phi0 = np.asarray(phi0, dtype=np.float64)
-    u0 = np.asarray(u0, dtype=np.float64)
+    phi0 = np.asarray(phi0, dtype=dtype)
+    u0 = np.asarray(u0, dtype=dtype)
     assert phi0.shape == _shape(P) and u0.shape == (P["dim"],) + _shape(P)
     fam = P["family"]
     rho = density(P, phi0)

@@ -5,12 +5,10 @@ Bars (Reading R15 metric, max|a - b| / max|b|):
     (FP16/BF16 storage: within the 16-bit encoding of the written deviation);
   * 1000 steps on laminar cases, ragged grids spanning several tiles and
     chunks, all four families, periodic / resting walls / moving walls / 3D:
-    phi and u within 1e-5 -- or, where the model amplifies FP32 rounding
-    beyond that (the conservative counter flux follows the direction of
-    near-zero gradients; the Cahn-Hilliard potential is a near-cancellation at
-    equilibrium), within 10x the FP64 oracle's own response to rounding its
-    populations to FP32 once per step (FP32 arithmetic rounds each stored
-    value about ten times per step), measured in the test;
+    phi and u within 1e-5 -- or, where the FP32 floor of the model on that
+    case is higher (rounding repeats coherently in quasi-steady flow), within
+    3x the deviation of the same equations evaluated in FP32 by the oracle,
+    measured in the test;
   * observables, sum(phi) conservation, save/load continuation, instability
     status.
 """
