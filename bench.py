@@ -12,7 +12,10 @@ W = 4, We = 5, density ratio 1, linear forcing, conservative Allen-Cahn
                step's observables, final phi copied back to the host
   roofline     algorithmic bytes/LU x cells / kernel time against the measured
                HBM copy bandwidth
-  variants     FP16 / BF16 deviation storage of the same workload
+  variants     FP16 / BF16 deviation storage of the same workload, and the
+               batched form: 512 2D droplet-in-shear domains (sizes uniform in
+               {64,128,256,512}^2, the four families mixed) in one persistent
+               launch per step, autotuned launch shape, CUDA-graph replay
   cpu_baseline the FP64 oracle on a bounded sample, host cores
 
 --impl reference times the FP64 oracle (the only reference this method has)
@@ -172,6 +175,54 @@ def e2e_run(P, phi_host, u_host, steps, world):
     return t1 - t0
 
 
+def batched_variant(steps, warmup, peak, count=512):
+    """The batched sweep: ``count`` moving-wall channels with a droplet, L
+    uniform in {64, 128, 256, 512}, Ca ~ U[0.05, 0.5], M ~ U[0.01, 0.2],
+    W in {3, 4, 5}, family uniform over the four; FP32; one persistent launch
+    per step (plus the gamma pre-pass when nonlocal domains are present),
+    launch shape from the autotuner, steps replayed as CUDA graphs."""
+    import numpy as np
+    import torch
+    from paper_2511_11360_gb300 import cases as C
+    from paper_2511_11360_gb300 import pflb
+    specs = C.batched_shear_sweep(count=count)
+    doms = [C.shear_instance(s["L"], s["family"], s["Ca"], s["M"], s["W"]) for s in specs]
+    stream = torch.cuda.current_stream()
+    b = pflb.Batch([P for P, _, _ in doms], stream=stream)
+    for i, (_, phi, u) in enumerate(doms):
+        b.init(i, np.asarray(phi, np.float32), np.asarray(u, np.float32))
+    del doms
+    tune = b.autotune(steps_per_trial=3)
+    b.set_graph(True)
+    b.step(warmup)
+    b.sync()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    status = "ok"
+    try:
+        b.sync()
+    except pflb.PflbError as ex:
+        status = str(ex)
+    cells, nbytes = b.cells(), b.bytes_per_step()
+    b.close()
+    fams = [0, 0, 0, 0]
+    for s in specs:
+        fams[s["family"]] += 1
+    return {"value": cells * steps / t / 1e9, "unit": "GLUPS", "instances": count, "cells": cells,
+            "bytes_per_lu": nbytes / cells, "roofline_frac": nbytes / (t / steps) / 1e9 / peak,
+            "ms_per_step": t / steps * 1e3, "launch": tune, "graph": True,
+            "families": {"fakhari2017": fams[0], "chai2018": fams[1], "hu2019": fams[2], "liang2014": fams[3]},
+            "status": status,
+            "err_vs_oracle": "each domain bitwise the single-domain step (nonlocal gamma: FP64 sum order); "
+                             "sampled domains vs FP64 oracle as the 2D fp32 path (tests/test_gpu_batch.py)"}
+
+
 def cpu_baseline(seconds_target=15.0):
     """The FP64 oracle, unmodified, on a bounded sample of the workload: a
     periodic 64^3 box of the same recipe (2 droplets of R = 16, W = 4,
@@ -237,6 +288,7 @@ def main():
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -305,6 +357,9 @@ def main():
             variants[name] = {"value": cells * args.steps * world / t2 / 1e9, "unit": "GLUPS",
                               "bytes_per_lu": b2, "roofline_frac": b2 * cells / (t2 / args.steps) / 1e9 / peak,
                               "ms_per_step": t2 / args.steps * 1e3}
+
+        if not args.no_batched:
+            variants["batched_2d_shear_512"] = batched_variant(args.steps, args.warmup, peak)
 
     # ---- end to end through the C ABI with host buffers
     phi_h = torch.empty(phi.shape, dtype=torch.float32, pin_memory=True)

@@ -190,6 +190,100 @@ int pflb_destroy(pflb_handle* h);
 const char* pflb_last_error(const pflb_handle* h);
 
 /* ---------------------------------------------------------------------------
+ * Batched step: many independent 2D domains in one persistent launch.
+ *
+ * A batch owns n domains (pflb_handle each) of any size, family and
+ * parameters -- a parameter sweep such as the four-family comparisons of
+ * Secs. III and IV -- and advances all of them one time level per kernel launch.
+ * Every (domain, tile) pair is an entry of a work list that resident blocks
+ * claim from an atomic counter, so domains of uneven size share the GPU
+ * without one launch per domain. Each domain's per-cell update is the one of
+ * pflb_step: a domain advanced in a batch has bitwise the same state as the
+ * same domain advanced alone; its observables agree up to the order of the
+ * FP64 sums (the nonlocal gamma of Chai2018/Hu2019 likewise).
+ *
+ * Restrictions: dim = 2 and FP32 storage for every domain (PFLB_EINVAL
+ * otherwise). Each domain keeps an observables ring of 2 records (the
+ * obs_capacity field is overridden).
+ *
+ * The domains are ordinary handles: pflb_batch_domain() returns domain i,
+ * on which pflb_init, pflb_get_fields, pflb_observables, pflb_save,
+ * pflb_load, pflb_obs_history and even pflb_step may be called (the batch
+ * notices a domain advanced on its own). The batch destroys them; never
+ * call pflb_destroy on one. All work is issued on the batch's stream (given
+ * at creation; every domain uses it).
+ * ------------------------------------------------------------------------- */
+typedef struct pflb_batch pflb_batch;
+
+/* Launch shape of the batched step. tile_a: cells per tile (and threads per
+ * block) along x, one of 64, 128, 256. chunk: rows per tile along y (>= 1).
+ * blocks_per_sm: resident blocks per SM of the persistent grid (0 = as many
+ * as fit). ms_per_step: the measured time of one batched step (autotuner
+ * output; ignored on input). from_cache: 1 if the autotuner read the shape
+ * from its cache file. */
+typedef struct pflb_batch_launch {
+  int32_t tile_a, chunk, blocks_per_sm, from_cache;
+  double ms_per_step;
+} pflb_batch_launch;
+
+/* Create n domains from params[0..n) (host array). Each needs dim = 2,
+ * storage = PFLB_FP32. On error *out may still receive a batch that carries
+ * the message (read it with pflb_batch_last_error, then destroy it). */
+int pflb_batch_create(const pflb_params* params, int32_t n, void* cuda_stream, pflb_batch** out);
+
+/* Number of domains, and domain i (0 <= i < n; NULL when out of range). */
+int32_t pflb_batch_size(const pflb_batch* b);
+pflb_handle* pflb_batch_domain(pflb_batch* b, int32_t i);
+
+/* Initialise domain i as pflb_init does (host or device phi0, u0). */
+int pflb_batch_init(pflb_batch* b, int32_t i, const float* phi0, const float* u0);
+
+/* Advance every domain nsteps time levels. Asynchronous on the batch's
+ * stream. Every domain must have been initialised. */
+int pflb_batch_step(pflb_batch* b, int64_t nsteps);
+
+/* Replay the step through CUDA graphs (on = 1) or launch it directly (0,
+ * the default). With graphs, the launches of two consecutive steps (the
+ * gamma pre-pass where the batch holds nonlocal/hybrid domains, then the
+ * persistent step kernel, twice) are captured once on an internal stream
+ * and replayed; the batch's stream waits for the replay through events. */
+int pflb_batch_set_graph(pflb_batch* b, int32_t on);
+
+/* Set / read the launch shape (see pflb_batch_launch). */
+int pflb_batch_set_launch(pflb_batch* b, const pflb_batch_launch* cfg);
+int pflb_batch_get_launch(const pflb_batch* b, pflb_batch_launch* out);
+
+/* Choose the launch shape by timing candidate shapes (tile_a in {64, 128,
+ * 256}, chunk in {4, 8, 16, 32}, blocks_per_sm in {all that fit, half})
+ * over steps_per_trial steps each (>= 1), then restore every domain's state
+ * and observables bit for bit, so tuning does not advance the batch.
+ * cache_path (may be NULL): a text file keyed by the device and the batch's
+ * (size, family) list; a matching line is used without timing, a new result
+ * is appended. The chosen shape is applied and written to *out (may be
+ * NULL). Synchronises the stream. */
+int pflb_batch_autotune(pflb_batch* b, int32_t steps_per_trial, const char* cache_path,
+                        pflb_batch_launch* out);
+
+/* The observables each domain recorded during its most recent step (as the
+ * last record of pflb_obs_history), for all n domains: out is a host array
+ * of n pflb_obs. Synchronises the stream. Returns PFLB_EUNSTABLE if any
+ * domain's record has that status. */
+int pflb_batch_observables(pflb_batch* b, pflb_obs* out);
+
+/* Synchronise the batch's stream; PFLB_EUNSTABLE if the most recent step of
+ * any domain flagged rho <= 0 or a non-finite phi or u. */
+int pflb_batch_sync(pflb_batch* b);
+
+/* Cells of all domains (one batched step performs this many lattice
+ * updates), and the algorithmic device-memory bytes of one batched step
+ * (the sum over domains of pflb_bytes_per_update x cells). */
+int64_t pflb_batch_cells(const pflb_batch* b);
+double pflb_batch_bytes_per_step(const pflb_batch* b);
+
+int pflb_batch_destroy(pflb_batch* b);
+const char* pflb_batch_last_error(const pflb_batch* b);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free phase-field sums. (The paper has no counterpart: this is a
  * service of the library for callers that cannot allocate device memory.)
  *

@@ -8,34 +8,13 @@
 #include <vector>
 
 #include "../../include/pflb.h"
-#include "pflb_args.h"
+#include "pflb_internal.h"
 
 using namespace pflb;
 
-struct pflb_handle {
-  pflb_params prm;
-  DevParams dp;
-  cudaStream_t stream = nullptr;
-  int dim = 2, QG = 9, QF = 9, storage = 0, family = 0;
-  long long N = 0;
-  size_t elem = 4;
-  void* g[2] = {nullptr, nullptr};
-  void* f = nullptr;
-  float* phiu = nullptr;
-  DevObs* obs = nullptr;      // ring of obs_cap slots + 1 slot for read-only passes
-  int obs_cap = 2;
-  double* gamma_acc = nullptr; // 3 pairs: step ring (2) + read-only pass (1)
-  float* scratch = nullptr;    // N*(d+2) floats, for host-side transfers
-  long long step = 0;
-  int cur = 0;                 // index of the source g array
-  int chunk = 0;
-  int status = PFLB_OK;
-  char err[512] = {0};
-};
+namespace pflb {
 
-namespace {
-
-int fail(pflb_handle* h, int code, const char* fmt, ...) {
+int handle_fail(pflb_handle* h, int code, const char* fmt, ...) {
   if (h) {
     va_list ap;
     va_start(ap, fmt);
@@ -46,19 +25,25 @@ int fail(pflb_handle* h, int code, const char* fmt, ...) {
   return code;
 }
 
-#define CU(h, call)                                                                    \
-  do {                                                                                 \
-    cudaError_t e_ = (call);                                                           \
-    if (e_ != cudaSuccess)                                                             \
-      return fail((h), PFLB_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
-  } while (0)
-
 int num_sms() {
   int dev = 0, n = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;
   cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
   return n > 0 ? n : 1;
 }
+
+bool handle_nonlocal(const pflb_handle* h) { return h->family == 1 || h->family == 2; }
+
+}  // namespace pflb
+
+namespace {
+
+#define CU(h, call)                                                                    \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return handle_fail((h), PFLB_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+  } while (0)
 
 // Tile shape of the fused kernel (mirrors Geom<DIM> in pflb_step.cuh).
 void tile_of(int dim, int& ta, int& tb) {
@@ -176,8 +161,6 @@ void init_launch(int fam, int dim, int storage, const InitArgs& a, cudaStream_t 
   }
 }
 
-bool nonlocal(const pflb_handle* h) { return h->family == 1 || h->family == 2; }
-
 int ensure_scratch(pflb_handle* h) {
   if (h->scratch) return PFLB_OK;
   const long long n = h->N * (h->dim + 2);
@@ -194,7 +177,22 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-StepArgs base_step_args(pflb_handle* h) {
+}  // namespace
+
+void pflb::obs_to_host(const DevObs& d, long long step, pflb_obs* o) {
+  o->step = step;
+  o->sum_phi = d.sum_phi;
+  o->vol_smooth = d.vol_smooth;
+  o->vol_count = (int64_t)d.vol_count;
+  o->ke = d.ke;
+  o->phi_max = key_float(d.phi_max_key);
+  o->phi_min = key_float(d.phi_min_key);
+  for (int k = 0; k < 3; ++k) o->centroid[k] = d.vol_smooth != 0.0 ? d.cen[k] / d.vol_smooth : 0.0;
+  o->status = d.status ? PFLB_EUNSTABLE : PFLB_OK;
+  o->pad = 0;
+}
+
+StepArgs pflb::handle_step_args(const pflb_handle* h) {
   StepArgs a;
   memset(&a, 0, sizeof(a));
   a.p = h->dp;
@@ -208,6 +206,8 @@ StepArgs base_step_args(pflb_handle* h) {
   return a;
 }
 
+namespace {
+
 // A read-only pass over the current state: fields to device buffers and the
 // observables into the extra ring slot.
 int macro_pass(pflb_handle* h, float* phi, float* u, float* p) {
@@ -220,14 +220,14 @@ int macro_pass(pflb_handle* h, float* phi, float* u, float* p) {
     return o;
   }();
   CU(h, cudaMemcpyAsync(slot, &init, sizeof(DevObs), cudaMemcpyHostToDevice, h->stream));
-  StepArgs a = base_step_args(h);
+  StepArgs a = handle_step_args(h);
   a.obs_slot = slot;
   a.obs_zero = nullptr;
   a.macro = 1;
   a.out_phi = phi;
   a.out_u = u;
   a.out_p = p;
-  if (nonlocal(h)) {
+  if (handle_nonlocal(h)) {
     double* acc = h->gamma_acc + 4;
     CU(h, cudaMemsetAsync(acc, 0, 2 * sizeof(double), h->stream));
     GammaArgs ga;
@@ -244,18 +244,6 @@ int macro_pass(pflb_handle* h, float* phi, float* u, float* p) {
   return PFLB_OK;
 }
 
-void to_obs(const DevObs& d, long long step, pflb_obs* o) {
-  o->step = step;
-  o->sum_phi = d.sum_phi;
-  o->vol_smooth = d.vol_smooth;
-  o->vol_count = (int64_t)d.vol_count;
-  o->ke = d.ke;
-  o->phi_max = key_float(d.phi_max_key);
-  o->phi_min = key_float(d.phi_min_key);
-  for (int k = 0; k < 3; ++k) o->centroid[k] = d.vol_smooth != 0.0 ? d.cen[k] / d.vol_smooth : 0.0;
-  o->status = d.status ? PFLB_EUNSTABLE : PFLB_OK;
-  o->pad = 0;
-}
 
 }  // namespace
 
@@ -296,7 +284,7 @@ int pflb_create(const pflb_params* params, void* cuda_stream, pflb_handle** out)
   auto alloc = [&](void** p, size_t bytes) -> int {
     if (cudaMalloc(p, bytes) != cudaSuccess) {
       cudaGetLastError();
-      return fail(h, PFLB_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
+      return handle_fail(h, PFLB_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
     }
     return PFLB_OK;
   };
@@ -310,7 +298,7 @@ int pflb_create(const pflb_params* params, void* cuda_stream, pflb_handle** out)
 }
 
 int pflb_init(pflb_handle* h, const float* phi0, const float* u0) {
-  if (!h || !phi0) return fail(h, PFLB_EINVAL, "null argument");
+  if (!h || !phi0) return handle_fail(h, PFLB_EINVAL, "null argument");
   if (h->status != PFLB_OK && h->status != PFLB_EUNSTABLE) return h->status;
   int rc = ensure_scratch(h);
   if (rc) return rc;
@@ -338,19 +326,20 @@ int pflb_init(pflb_handle* h, const float* phi0, const float* u0) {
   CU(h, cudaStreamSynchronize(h->stream));
   h->cur = 0;
   h->step = 0;
+  h->initialized = 1;
   h->status = PFLB_OK;
   h->err[0] = 0;
   return PFLB_OK;
 }
 
 int pflb_step(pflb_handle* h, int64_t nsteps) {
-  if (!h || nsteps < 0) return fail(h, PFLB_EINVAL, "invalid argument");
+  if (!h || nsteps < 0) return handle_fail(h, PFLB_EINVAL, "invalid argument");
   if (h->status != PFLB_OK && h->status != PFLB_EUNSTABLE) return h->status;
   for (int64_t i = 0; i < nsteps; ++i) {
-    StepArgs a = base_step_args(h);
+    StepArgs a = handle_step_args(h);
     a.obs_slot = h->obs + (h->step % h->obs_cap);
     a.obs_zero = h->obs + ((h->step + 1) % h->obs_cap);
-    if (nonlocal(h)) {
+    if (handle_nonlocal(h)) {
       double* acc = h->gamma_acc + 2 * (h->step & 1);
       GammaArgs ga;
       ga.p = h->dp;
@@ -380,7 +369,7 @@ int pflb_sync(pflb_handle* h) {
     for (long long i = 0; i < n; ++i) {
       const long long s = h->step - 1 - i;
       if (o[s % h->obs_cap].status) {
-        return fail(h, PFLB_EUNSTABLE, "step %lld produced rho <= 0 or non-finite phi/u", s);
+        return handle_fail(h, PFLB_EUNSTABLE, "step %lld produced rho <= 0 or non-finite phi/u", s);
       }
     }
   }
@@ -388,7 +377,7 @@ int pflb_sync(pflb_handle* h) {
 }
 
 int pflb_observables(pflb_handle* h, pflb_obs* out) {
-  if (!h || !out) return fail(h, PFLB_EINVAL, "null argument");
+  if (!h || !out) return handle_fail(h, PFLB_EINVAL, "null argument");
   int rc = ensure_scratch(h);
   if (rc) return rc;
   rc = macro_pass(h, h->scratch, h->scratch + h->N, h->scratch + (long long)(h->dim + 1) * h->N);
@@ -396,13 +385,13 @@ int pflb_observables(pflb_handle* h, pflb_obs* out) {
   DevObs d;
   CU(h, cudaMemcpyAsync(&d, h->obs + h->obs_cap, sizeof(DevObs), cudaMemcpyDeviceToHost, h->stream));
   CU(h, cudaStreamSynchronize(h->stream));
-  to_obs(d, h->step, out);
-  if (out->status != PFLB_OK) fail(h, PFLB_EUNSTABLE, "state has rho <= 0 or non-finite phi/u");
+  obs_to_host(d, h->step, out);
+  if (out->status != PFLB_OK) handle_fail(h, PFLB_EUNSTABLE, "state has rho <= 0 or non-finite phi/u");
   return h->status;
 }
 
 int pflb_obs_history(pflb_handle* h, pflb_obs* out, int32_t n, int32_t* written) {
-  if (!h || !out || n < 0) return fail(h, PFLB_EINVAL, "invalid argument");
+  if (!h || !out || n < 0) return handle_fail(h, PFLB_EINVAL, "invalid argument");
   long long m = n;
   if (m > h->step) m = h->step;
   if (m > h->obs_cap - 1) m = h->obs_cap - 1;  // the newest slot may be in flight-zeroed
@@ -411,7 +400,7 @@ int pflb_obs_history(pflb_handle* h, pflb_obs* out, int32_t n, int32_t* written)
   CU(h, cudaMemcpy(o.data(), h->obs, h->obs_cap * sizeof(DevObs), cudaMemcpyDeviceToHost));
   for (long long i = 0; i < m; ++i) {
     const long long s = h->step - m + i;
-    to_obs(o[s % h->obs_cap], s, &out[i]);
+    obs_to_host(o[s % h->obs_cap], s, &out[i]);
   }
   if (written) *written = (int32_t)m;
   return PFLB_OK;
@@ -457,7 +446,7 @@ static int canon(pflb_handle* h, float* state_dev, int to_canon) {
 }
 
 int pflb_save(pflb_handle* h, float* state) {
-  if (!h || !state) return fail(h, PFLB_EINVAL, "null argument");
+  if (!h || !state) return handle_fail(h, PFLB_EINVAL, "null argument");
   const size_t nb = (size_t)pflb_state_floats(h) * sizeof(float);
   if (is_device_ptr(state)) {
     int rc = canon(h, state, 1);
@@ -469,7 +458,7 @@ int pflb_save(pflb_handle* h, float* state) {
     if (rc == PFLB_OK) {
       cudaError_t e = cudaMemcpyAsync(state, tmp, nb, cudaMemcpyDeviceToHost, h->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-      if (e != cudaSuccess) rc = fail(h, PFLB_ECUDA, "copy of the state failed: %s", cudaGetErrorString(e));
+      if (e != cudaSuccess) rc = handle_fail(h, PFLB_ECUDA, "copy of the state failed: %s", cudaGetErrorString(e));
     }
     cudaFree(tmp);
     if (rc) return rc;
@@ -479,7 +468,7 @@ int pflb_save(pflb_handle* h, float* state) {
 }
 
 int pflb_load(pflb_handle* h, const float* state) {
-  if (!h || !state) return fail(h, PFLB_EINVAL, "null argument");
+  if (!h || !state) return handle_fail(h, PFLB_EINVAL, "null argument");
   const size_t nb = (size_t)pflb_state_floats(h) * sizeof(float);
   float* src = const_cast<float*>(state);
   float* tmp = nullptr;
@@ -488,7 +477,7 @@ int pflb_load(pflb_handle* h, const float* state) {
     cudaError_t e = cudaMemcpyAsync(tmp, state, nb, cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) {
       cudaFree(tmp);
-      return fail(h, PFLB_ECUDA, "copy of the state failed: %s", cudaGetErrorString(e));
+      return handle_fail(h, PFLB_ECUDA, "copy of the state failed: %s", cudaGetErrorString(e));
     }
     src = tmp;
   }
@@ -496,7 +485,7 @@ int pflb_load(pflb_handle* h, const float* state) {
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (tmp) cudaFree(tmp);
   if (rc) return rc;
-  if (e != cudaSuccess) return fail(h, PFLB_ECUDA, "load failed: %s", cudaGetErrorString(e));
+  if (e != cudaSuccess) return handle_fail(h, PFLB_ECUDA, "load failed: %s", cudaGetErrorString(e));
   return PFLB_OK;
 }
 
@@ -509,12 +498,12 @@ double pflb_bytes_per_update(const pflb_handle* h) {
   const int qg = (h->dim == 3 && h->family != 3) ? h->QG - 1 : h->QG;
   double b = 2.0 * (qg + h->QF) * (double)h->elem;
   if (h->family == 3) b += 2.0 * h->dim * 4.0;        // phi*u read + write
-  if (nonlocal(h)) b += (double)qg * h->elem;         // g read by the gamma reduction
+  if (handle_nonlocal(h)) b += (double)qg * h->elem;         // g read by the gamma reduction
   return b;
 }
 
 int pflb_set_chunk(pflb_handle* h, int32_t chunk) {
-  if (!h || chunk < 0) return fail(h, PFLB_EINVAL, "chunk must be >= 0");
+  if (!h || chunk < 0) return handle_fail(h, PFLB_EINVAL, "chunk must be >= 0");
   h->chunk = chunk;
   return PFLB_OK;
 }

@@ -22,6 +22,7 @@ struct StepArgs {
   float* out_p;
   int chunk;              // cells per block along the marching axis
   long long N;
+  double* gamma_next;     // nonlocal/hybrid: the next step's pair (zeroed by the batched pre-pass)
 };
 
 struct InitArgs {
@@ -54,6 +55,35 @@ struct CanonArgs {
   long long N;
 };
 
+// One tile of the batched step: instance, first cell along x, first row of
+// the chunk along y, family of the instance.
+struct BatchTile {
+  int inst, a0, c0, fam;
+};
+
+// A contiguous cell range of one nonlocal/hybrid instance for the batched
+// gamma pre-pass.
+struct BatchGammaEntry {
+  int inst, begin, end, pad;
+};
+
+struct BatchArgs {
+  const StepArgs* args;     // per instance: this step's arguments
+  const BatchTile* tiles;
+  int ntiles;
+  int ninst;
+  int chunk;                // rows per tile along y
+  unsigned* counter;        // tile claims of this step (zero at launch)
+  unsigned* counter_next;   // the next step's counter, reset here
+};
+
+struct BatchGammaArgs {
+  const StepArgs* args;
+  const BatchGammaEntry* ent;
+  int nent;
+  int ninst;
+};
+
 // Per-family translation units.
 void step_fakhari(int dim, int storage, const StepArgs& a, cudaStream_t s);
 void step_chai(int dim, int storage, const StepArgs& a, cudaStream_t s);
@@ -66,5 +96,11 @@ void init_liang2014(int dim, int storage, const InitArgs& a, cudaStream_t s);
 // pflb_aux.cu
 void gamma_sums(int dim, int storage, const GammaArgs& a, cudaStream_t s);
 void canon_copy(int dim, int storage, const CanonArgs& a, cudaStream_t s);
+// pflb_batch_kernels.cu (2D, FP32 storage)
+bool batch_tile_supported(int tile_a);
+int batch_max_blocks_per_sm(int tile_a);
+void batch_step(int tile_a, const BatchArgs& a, int grid, cudaStream_t s);
+void batch_gamma(const BatchGammaArgs& a, int grid, cudaStream_t s);
+void batch_obs_gather(const DevObs* const* src, DevObs* dst, int n, cudaStream_t s);
 
 }  // namespace pflb

@@ -1,0 +1,42 @@
+// Host-side state shared by the translation units of the C ABI: the handle of
+// one domain and the helpers the batch entry points reuse.
+#pragma once
+
+#include "../../include/pflb.h"
+#include "pflb_args.h"
+
+struct pflb_handle {
+  pflb_params prm;
+  pflb::DevParams dp;
+  cudaStream_t stream = nullptr;
+  int dim = 2, QG = 9, QF = 9, storage = 0, family = 0;
+  long long N = 0;
+  size_t elem = 4;
+  void* g[2] = {nullptr, nullptr};
+  void* f = nullptr;
+  float* phiu = nullptr;
+  pflb::DevObs* obs = nullptr;  // ring of obs_cap slots + 1 slot for read-only passes
+  int obs_cap = 2;
+  double* gamma_acc = nullptr;  // 3 pairs: step ring (2) + read-only pass (1)
+  float* scratch = nullptr;     // N*(d+2) floats, for host-side transfers
+  long long step = 0;
+  int cur = 0;                  // index of the source g array
+  int chunk = 0;
+  int initialized = 0;         // set by pflb_init
+  int status = PFLB_OK;
+  char err[512] = {0};
+};
+
+namespace pflb {
+
+int num_sms();
+// Nonlocal or hybrid Allen-Cahn (needs the global gamma pre-pass).
+bool handle_nonlocal(const pflb_handle* h);
+// Launch arguments of the next step of h (no observables slots set).
+StepArgs handle_step_args(const pflb_handle* h);
+// Host form of a device observables record.
+void obs_to_host(const DevObs& d, long long step, pflb_obs* o);
+// Records a message and a sticky status on h; returns code.
+int handle_fail(pflb_handle* h, int code, const char* fmt, ...);
+
+}  // namespace pflb

@@ -308,16 +308,34 @@ struct Cell {
 };
 
 // ---------------------------------------------------------------------------
-// The kernel.
+// Shared-memory footprint of one tile march.
 // ---------------------------------------------------------------------------
-template <int FAM, int DIM, typename T>
-__global__ void __launch_bounds__(Geom<DIM>::TA * Geom<DIM>::TB, Geom<DIM>::MINB)
-step_kernel(const StepArgs args) {
+template <int FAM, int DIM, int TA, int TB>
+struct TileSmem {
+  static constexpr bool CH = (FAM == FAM_LIANG);
+  static constexpr int H = CH ? 2 : 1;
+  static constexpr int HB = (DIM == 3) ? H : 0;
+  static constexpr int PLANE = (TA + 2 * H) * (TB + 2 * HB);
+  static constexpr int NSLOT = CH ? 8 : 4;
+  static constexpr int PHI = NSLOT * PLANE;
+  static constexpr int MU = CH ? 4 * (TA + 2) * (TB + 2 * ((DIM == 3) ? 1 : 0)) : 1;
+};
+
+// ---------------------------------------------------------------------------
+// One tile: the cells [a0, a0+TA) x [b0, b0+TB) marched over planes
+// [c0, min(c0+chunk, NC)) of the slow axis. Called by the single-domain
+// kernel (one tile per block) and by the persistent batch kernel (tiles of
+// many domains claimed in turn). Accumulates the observables into obs.
+// ---------------------------------------------------------------------------
+template <int FAM, int DIM, typename T, int TA, int TB>
+__device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, int c0, int chunk,
+                                          float* __restrict__ s_phi, float* __restrict__ s_mu,
+                                          ObsPartial& obs) {
   using LG = typename Lattices<DIM>::G;
   using LF = typename Lattices<DIM>::F;
   using LS = typename Lattices<DIM>::S;
   constexpr int QG = LG::Q, QF = LF::Q, QS = LS::Q;
-  constexpr int TA = Geom<DIM>::TA, TB = Geom<DIM>::TB, NT = TA * TB;
+  constexpr int NT = TA * TB;
   constexpr bool CH = (FAM == FAM_LIANG);
   constexpr int H = CH ? 2 : 1;                 // phi halo
   constexpr int HB = (DIM == 3) ? H : 0;
@@ -330,10 +348,7 @@ step_kernel(const StepArgs args) {
   constexpr int MSLOT = 4;
   constexpr int MHALO = MPLANE - NT;
   constexpr int KM = (MHALO + NT - 1) / NT;
-
-  __shared__ float s_phi[NSLOT * PLANE];
-  __shared__ float s_mu[CH ? MSLOT * MPLANE : 1];
-  __shared__ double s_red[(NT / 32) * 10];
+  (void)RB;
 
   const DevParams& P = args.p;
   const int NA = P.nx, NB = (DIM == 3) ? P.ny : 1, NC = (DIM == 3) ? P.nz : P.ny;
@@ -341,22 +356,12 @@ step_kernel(const StepArgs args) {
   // (the host rejects Q*N >= 2^32).
   const unsigned N = (unsigned)args.N;
   const int NAB = NA * NB;
-  const int tiles_a = (NA + TA - 1) / TA, tiles_b = (NB + TB - 1) / TB;
-  int bid = blockIdx.x;
-  const int ti = bid % tiles_a;
-  bid /= tiles_a;
-  const int tj = bid % tiles_b;
-  bid /= tiles_b;
-  const int a0 = ti * TA, b0 = tj * TB;
-  const int c0 = bid * args.chunk;
-  const int c1 = min(c0 + args.chunk, NC);
+  const int c1 = min(c0 + chunk, NC);
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = tx + TA * ty;
   const int a = a0 + tx, b = b0 + ty;
   const bool active = (a < NA) && (b < NB);
   const bool walls = P.walls != 0;
-
-  if (args.obs_zero != nullptr && blockIdx.x == 0 && tid == 0) obs_zero_slot(args.obs_zero);
 
   float gamma = 0.0f;
   if constexpr (FAM == FAM_CHAI || FAM == FAM_HU) {
@@ -475,9 +480,6 @@ step_kernel(const StepArgs args) {
       }
     }
   };
-
-  ObsPartial obs;
-  obs_init(obs);
 
   float g0[QG], g1[QG], g2[QG];
   // Prologue: planes c0-H .. c0+H-1.
@@ -654,6 +656,31 @@ step_kernel(const StepArgs args) {
     }
   }
 
+}
+
+// ---------------------------------------------------------------------------
+// The single-domain kernel: one tile per block.
+// ---------------------------------------------------------------------------
+template <int FAM, int DIM, typename T>
+__global__ void __launch_bounds__(Geom<DIM>::TA * Geom<DIM>::TB, Geom<DIM>::MINB)
+step_kernel(const StepArgs args) {
+  constexpr int TA = Geom<DIM>::TA, TB = Geom<DIM>::TB;
+  using SM = TileSmem<FAM, DIM, TA, TB>;
+  __shared__ float s_phi[SM::PHI];
+  __shared__ float s_mu[SM::MU];
+  __shared__ double s_red[(TA * TB / 32) * 10];
+  const int NA = args.p.nx, NB = (DIM == 3) ? args.p.ny : 1;
+  const int tiles_a = (NA + TA - 1) / TA, tiles_b = (NB + TB - 1) / TB;
+  int bid = blockIdx.x;
+  const int ti = bid % tiles_a;
+  bid /= tiles_a;
+  const int tj = bid % tiles_b;
+  bid /= tiles_b;
+  if (args.obs_zero != nullptr && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+    obs_zero_slot(args.obs_zero);
+  ObsPartial obs;
+  obs_init(obs);
+  step_tile<FAM, DIM, T, TA, TB>(args, ti * TA, tj * TB, bid * args.chunk, args.chunk, s_phi, s_mu, obs);
   obs_block_commit(obs, args.obs_slot, s_red);
 }
 

@@ -43,6 +43,15 @@ class Params(ctypes.Structure):
     ]
 
 
+class BatchLaunch(ctypes.Structure):
+    _fields_ = [("tile_a", ctypes.c_int32), ("chunk", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("from_cache", ctypes.c_int32), ("ms_per_step", ctypes.c_double)]
+
+    def to_dict(self):
+        return dict(tile_a=self.tile_a, chunk=self.chunk, blocks_per_sm=self.blocks_per_sm,
+                    from_cache=self.from_cache, ms_per_step=self.ms_per_step)
+
+
 class Obs(ctypes.Structure):
     _fields_ = [
         ("step", ctypes.c_int64), ("sum_phi", ctypes.c_double), ("vol_smooth", ctypes.c_double),
@@ -81,6 +90,23 @@ SIGNATURES = {
     "pflb_phase_sums_static": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_void_p, ctypes.POINTER(Obs),
                                               ctypes.c_void_p]),
     "pflb_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "pflb_batch_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int32, ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    "pflb_batch_size": (ctypes.c_int32, [ctypes.c_void_p]),
+    "pflb_batch_domain": (ctypes.c_void_p, [ctypes.c_void_p, ctypes.c_int32]),
+    "pflb_batch_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "pflb_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "pflb_batch_set_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "pflb_batch_set_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(BatchLaunch)]),
+    "pflb_batch_get_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(BatchLaunch)]),
+    "pflb_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_char_p,
+                                           ctypes.POINTER(BatchLaunch)]),
+    "pflb_batch_observables": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Obs)]),
+    "pflb_batch_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "pflb_batch_cells": (ctypes.c_int64, [ctypes.c_void_p]),
+    "pflb_batch_bytes_per_step": (ctypes.c_double, [ctypes.c_void_p]),
+    "pflb_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "pflb_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
 }
 
 
@@ -157,10 +183,18 @@ def make_params(d):
 class Sim:
     """One PF-LB domain on the current CUDA device (a pflb_handle)."""
 
-    def __init__(self, params, stream=None):
+    def __init__(self, params, stream=None, _borrowed=None):
         self.lib = load_library()
         self.params = dict(params)
         self._p = make_params(params)
+        self._owner = _borrowed is None
+        if _borrowed is not None:
+            # A domain of a Batch: the batch owns (and destroys) the handle.
+            self.h = ctypes.c_void_p(_borrowed)
+            self.dim = self._p.dim
+            self.shape = (self._p.ny, self._p.nx) if self.dim == 2 else (self._p.nz, self._p.ny, self._p.nx)
+            self.N = int(np.prod(self.shape))
+            return
         h = ctypes.c_void_p()
         rc = self.lib.pflb_create(ctypes.byref(self._p), _stream(stream), ctypes.byref(h))
         self.h = h
@@ -179,7 +213,7 @@ class Sim:
         return rc
 
     def close(self):
-        if self.h is not None and self.h.value:
+        if self.h is not None and self.h.value and getattr(self, "_owner", True):
             self.lib.pflb_destroy(self.h)
         self.h = ctypes.c_void_p()
 
@@ -249,6 +283,94 @@ class Sim:
         if isinstance(state, np.ndarray):
             state = np.ascontiguousarray(state, dtype=np.float32)
         return self._check(self.lib.pflb_load(self.h, _ptr(state)))
+
+
+class Batch:
+    """Many 2D domains advanced by one persistent launch per step (a
+    pflb_batch). ``params_list``: one parameter dictionary per domain (2D,
+    FP32 storage). ``domain(i)`` gives a Sim view of domain i (owned by the
+    batch) for init, fields, observables, save and load."""
+
+    def __init__(self, params_list, stream=None):
+        self.lib = load_library()
+        self.params = [dict(p) for p in params_list]
+        arr = (Params * len(self.params))(*[make_params(p) for p in self.params])
+        self._arr = arr
+        b = ctypes.c_void_p()
+        rc = self.lib.pflb_batch_create(arr, len(self.params), _stream(stream), ctypes.byref(b))
+        self.b = b
+        if rc != PFLB_OK:
+            msg = self.lib.pflb_batch_last_error(b).decode() if b.value else "batch create failed"
+            self.lib.pflb_batch_destroy(b)
+            self.b = ctypes.c_void_p()
+            raise PflbError(rc, msg)
+        self.n = len(self.params)
+        self._views = [None] * self.n
+
+    def _check(self, rc):
+        if rc != PFLB_OK:
+            raise PflbError(rc, self.lib.pflb_batch_last_error(self.b).decode())
+        return rc
+
+    def close(self):
+        for v in self._views:
+            if v is not None:
+                v.h = ctypes.c_void_p()
+        if self.b is not None and self.b.value:
+            self.lib.pflb_batch_destroy(self.b)
+        self.b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def domain(self, i):
+        if self._views[i] is None:
+            h = self.lib.pflb_batch_domain(self.b, int(i))
+            if not h:
+                raise IndexError(i)
+            self._views[i] = Sim(self.params[i], _borrowed=h)
+        return self._views[i]
+
+    def init(self, i, phi0, u0=None):
+        return self.domain(i).init(phi0, u0)
+
+    def step(self, n=1):
+        return self._check(self.lib.pflb_batch_step(self.b, int(n)))
+
+    def sync(self):
+        return self._check(self.lib.pflb_batch_sync(self.b))
+
+    def set_graph(self, on):
+        return self._check(self.lib.pflb_batch_set_graph(self.b, 1 if on else 0))
+
+    def set_launch(self, tile_a, chunk, blocks_per_sm=0):
+        c = BatchLaunch(int(tile_a), int(chunk), int(blocks_per_sm), 0, 0.0)
+        return self._check(self.lib.pflb_batch_set_launch(self.b, ctypes.byref(c)))
+
+    def launch(self):
+        c = BatchLaunch()
+        self._check(self.lib.pflb_batch_get_launch(self.b, ctypes.byref(c)))
+        return c.to_dict()
+
+    def autotune(self, steps_per_trial=3, cache_path=None):
+        c = BatchLaunch()
+        path = cache_path.encode() if cache_path else None
+        self._check(self.lib.pflb_batch_autotune(self.b, int(steps_per_trial), path, ctypes.byref(c)))
+        return c.to_dict()
+
+    def observables(self):
+        arr = (Obs * self.n)()
+        self._check(self.lib.pflb_batch_observables(self.b, arr))
+        return [arr[i].to_dict() for i in range(self.n)]
+
+    def cells(self):
+        return int(self.lib.pflb_batch_cells(self.b))
+
+    def bytes_per_step(self):
+        return float(self.lib.pflb_batch_bytes_per_step(self.b))
 
 
 def lattice(dim, which):

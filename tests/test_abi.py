@@ -74,3 +74,39 @@ def test_no_device_is_an_error_not_a_fallback(lib):
     with pytest.raises(pflb.PflbError) as ei:
         pflb.Sim(cases.params(dim=2, nx=16, ny=12))
     assert ei.value.code == pflb.PFLB_ECUDA
+
+
+@pytest.mark.parametrize("bad", [dict(dim=3, nz=8), dict(storage=1), dict(storage=2)])
+def test_batch_rejects_unsupported_domains(lib, bad):
+    good = cases.params(dim=2, nx=16, ny=12)
+    d = dict(good)
+    d.update(bad)
+    p = pflb.make_params(d)
+    if d["dim"] == 3:
+        p.nz = int(d["nz"])
+    arr = (pflb.Params * 2)(pflb.make_params(good), p)
+    b = ctypes.c_void_p()
+    rc = lib.pflb_batch_create(arr, 2, None, ctypes.byref(b))
+    try:
+        assert rc == pflb.PFLB_EINVAL
+        assert b"domain 1" in lib.pflb_batch_last_error(b)
+    finally:
+        lib.pflb_batch_destroy(b)
+
+
+def test_batch_needs_domains(lib):
+    b = ctypes.c_void_p()
+    rc = lib.pflb_batch_create(None, 0, None, ctypes.byref(b))
+    try:
+        assert rc == pflb.PFLB_EINVAL
+    finally:
+        lib.pflb_batch_destroy(b)
+
+
+def test_batch_without_device_is_an_error(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(pflb.PflbError) as ei:
+        pflb.Batch([cases.params(dim=2, nx=16, ny=12)])
+    assert ei.value.code == pflb.PFLB_ECUDA
