@@ -45,14 +45,9 @@ namespace {
       return handle_fail((h), PFLB_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
   } while (0)
 
-// Tile shape of the fused kernel (mirrors Geom<DIM> in pflb_step.cuh).
-void tile_of(int dim, int& ta, int& tb) {
-  if (dim == 3) { ta = 32; tb = 8; } else { ta = 128; tb = 1; }
-}
-
 int default_chunk(const pflb_handle* h) {
-  int ta, tb;
-  tile_of(h->dim, ta, tb);
+  const TileShape ts = tile_shape(h->family, h->dim, h->storage);
+  const int ta = ts.ta, tb = ts.tb;
   const int NA = h->prm.nx, NB = h->dim == 3 ? h->prm.ny : 1, NC = h->dim == 3 ? h->prm.nz : h->prm.ny;
   const long long tiles = (long long)((NA + ta - 1) / ta) * ((NB + tb - 1) / tb);
   const long long target = 8LL * num_sms();

@@ -21,9 +21,11 @@ struct BatchGeom {
 
 template <int TA>
 __global__ void __launch_bounds__(TA, BatchGeom<TA>::MINB) batch_step_kernel(const BatchArgs ba) {
-  using SMX = TileSmem<FAM_LIANG, 2, TA, 1>;  // the largest footprint of the four families
-  __shared__ float s_phi[SMX::PHI];
-  __shared__ float s_mu[SMX::MU];
+  using SMX = TileSmem<FAM_LIANG, 2, float, TA, 1>;  // the largest footprint of the four families
+  extern __shared__ __align__(16) float dyn_smem[];
+  float* s_stage = dyn_smem;
+  float* s_phi = dyn_smem + SMX::STAGE;
+  float* s_mu = s_phi + SMX::PHI;
   __shared__ double s_red[(TA / 32) * 10];
   __shared__ __align__(16) StepArgs s_args;
   __shared__ int s_tile;
@@ -52,16 +54,16 @@ __global__ void __launch_bounds__(TA, BatchGeom<TA>::MINB) batch_step_kernel(con
     obs_init(obs);
     switch (e.fam) {
       case FAM_FAKHARI:
-        step_tile<FAM_FAKHARI, 2, float, TA, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, obs);
+        step_tile<FAM_FAKHARI, 2, float, TA, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
         break;
       case FAM_CHAI:
-        step_tile<FAM_CHAI, 2, float, TA, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, obs);
+        step_tile<FAM_CHAI, 2, float, TA, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
         break;
       case FAM_HU:
-        step_tile<FAM_HU, 2, float, TA, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, obs);
+        step_tile<FAM_HU, 2, float, TA, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
         break;
       default:
-        step_tile<FAM_LIANG, 2, float, TA, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, obs);
+        step_tile<FAM_LIANG, 2, float, TA, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
         break;
     }
     obs_block_commit(obs, s_args.obs_slot, s_red);
@@ -129,9 +131,18 @@ __global__ void obs_gather_kernel(const DevObs* const* src, DevObs* dst, int n) 
 bool batch_tile_supported(int tile_a) { return tile_a == 64 || tile_a == 128 || tile_a == 256; }
 
 template <int TA>
+static size_t batch_smem() {
+  constexpr size_t smem = TileSmem<FAM_LIANG, 2, float, TA, 1>::BYTES;
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(batch_step_kernel<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  (void)attr;
+  return smem;
+}
+
+template <int TA>
 static int max_blocks() {
   int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_step_kernel<TA>, TA, 0) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_step_kernel<TA>, TA, batch_smem<TA>()) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
@@ -148,9 +159,9 @@ int batch_max_blocks_per_sm(int tile_a) {
 
 void batch_step(int tile_a, const BatchArgs& a, int grid, cudaStream_t s) {
   switch (tile_a) {
-    case 64: batch_step_kernel<64><<<grid, 64, 0, s>>>(a); break;
-    case 128: batch_step_kernel<128><<<grid, 128, 0, s>>>(a); break;
-    default: batch_step_kernel<256><<<grid, 256, 0, s>>>(a); break;
+    case 64: batch_step_kernel<64><<<grid, 64, batch_smem<64>(), s>>>(a); break;
+    case 128: batch_step_kernel<128><<<grid, 128, batch_smem<128>(), s>>>(a); break;
+    default: batch_step_kernel<256><<<grid, 256, batch_smem<256>(), s>>>(a); break;
   }
 }
 

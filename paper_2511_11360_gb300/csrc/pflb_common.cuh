@@ -206,6 +206,18 @@ template <> struct Codec<__nv_bfloat16> {
 };
 
 // Population slot q of lattice L at p, rest-state constant c.
+// Asynchronous 4-byte global -> shared copies (cp.async, L1-allocating),
+// completed per thread by cp.async.wait_group.
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
+
 template <typename T, typename L>
 __device__ __forceinline__ float pop_load(const T* p, int q, float c) {  // read-only data
   return Codec<T>::dec(Codec<T>::ld(p), pow2_scale<L>(q), wprime<L>(q) * c);

@@ -15,14 +15,20 @@
 // Halfway bounce-back walls (2D, y ends) reflect into the cell's own slots.
 #pragma once
 
+#include <type_traits>
+
 #include "pflb_args.h"
 #include "pflb_symsum.cuh"
 
 namespace pflb {
 
-template <int DIM> struct Geom;
-template <> struct Geom<3> { static constexpr int TA = 32, TB = 8, MINB = 2; };
-template <> struct Geom<2> { static constexpr int TA = 128, TB = 1, MINB = 4; };
+template <int FAM, int DIM, typename T>
+struct Geom {
+  static constexpr int STORAGE = std::is_same<T, float>::value ? 0 : 1;
+  static constexpr int TA = tile_shape(FAM, DIM, STORAGE).ta;
+  static constexpr int TB = tile_shape(FAM, DIM, STORAGE).tb;
+  static constexpr int MINB = tile_shape(FAM, DIM, STORAGE).minb;
+};
 
 
 
@@ -310,15 +316,23 @@ struct Cell {
 // ---------------------------------------------------------------------------
 // Shared-memory footprint of one tile march.
 // ---------------------------------------------------------------------------
-template <int FAM, int DIM, int TA, int TB>
+template <int FAM, int DIM, typename T, int TA, int TB>
 struct TileSmem {
   static constexpr bool CH = (FAM == FAM_LIANG);
   static constexpr int H = CH ? 2 : 1;
   static constexpr int HB = (DIM == 3) ? H : 0;
+  static constexpr int NT = TA * TB;
   static constexpr int PLANE = (TA + 2 * H) * (TB + 2 * HB);
   static constexpr int NSLOT = CH ? 8 : 4;
   static constexpr int PHI = NSLOT * PLANE;
   static constexpr int MU = CH ? 4 * (TA + 2) * (TB + 2 * ((DIM == 3) ? 1 : 0)) : 1;
+  // FP32 storage stages the next plane's populations asynchronously: two
+  // stages of f (Q_f per cell) and g (Q_g per cell of the tile and halo).
+  static constexpr bool STAGED = std::is_same<T, float>::value;
+  static constexpr int FST = Lattices<DIM>::F::Q * NT;
+  static constexpr int GST = Lattices<DIM>::G::Q * PLANE;
+  static constexpr int STAGE = STAGED ? 2 * (FST + GST) : 0;
+  static constexpr size_t BYTES = (size_t)(STAGE + PHI + MU) * sizeof(float);
 };
 
 // ---------------------------------------------------------------------------
@@ -330,7 +344,7 @@ struct TileSmem {
 template <int FAM, int DIM, typename T, int TA, int TB>
 __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, int c0, int chunk,
                                           float* __restrict__ s_phi, float* __restrict__ s_mu,
-                                          ObsPartial& obs) {
+                                          float* __restrict__ s_stage, ObsPartial& obs) {
   using LG = typename Lattices<DIM>::G;
   using LF = typename Lattices<DIM>::F;
   using LS = typename Lattices<DIM>::S;
@@ -348,6 +362,9 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
   constexpr int MSLOT = 4;
   constexpr int MHALO = MPLANE - NT;
   constexpr int KM = (MHALO + NT - 1) / NT;
+  constexpr bool STAGED = TileSmem<FAM, DIM, T, TA, TB>::STAGED;
+  constexpr int FST = TileSmem<FAM, DIM, T, TA, TB>::FST, GST = TileSmem<FAM, DIM, T, TA, TB>::GST;
+  constexpr bool SKIP0 = (DIM == 3 && !CH);   // D3Q7 rest slot of the AC families: w_0 = 0, g_0 = 0
   (void)RB;
 
   const DevParams& P = args.p;
@@ -481,6 +498,71 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
     }
   };
 
+  // Own-cell neighbour coordinates along the fast axes (constant).
+  const int aw = (a < NA) ? a : 0, bw = (b < NB) ? b : 0;
+  const int am = aw == 0 ? NA - 1 : aw - 1, ap = aw == NA - 1 ? 0 : aw + 1;
+  const int bm = bw == 0 ? NB - 1 : bw - 1, bp = bw == NB - 1 ? 0 : bw + 1;
+  const int rbm = bm * NA, rbw = bw * NA, rbp = bp * NA;
+  auto A_of = [&](int d) { return d < 0 ? am : (d > 0 ? ap : aw); };
+  auto RB_of = [&](int d) { return d < 0 ? rbm : (d > 0 ? rbp : rbw); };
+
+  // Element offset of the f population q the own cell reads at plane c (AA
+  // pattern): even steps its own slot q; odd steps slot opp(q) of x - e_q,
+  // or its own slot q where x - e_q lies beyond a wall.
+  auto f_read_ofs = [&](int c, int q) -> unsigned {
+    const int da = da_of<DIM, LF>(q), db = db_of<DIM, LF>(q), dc = dc_of<DIM, LF>(q);
+    const bool cross = walls && ((dc > 0 && c == 0) || (dc < 0 && c == NC - 1));
+    if (args.parity == 0 || cross) return q * N + (unsigned)(aw + rbw + c * NAB);
+    const int cs = dc > 0 ? (c == 0 ? NC - 1 : c - 1) : (dc < 0 ? (c == NC - 1 ? 0 : c + 1) : c);
+    return LF::opp(q) * N + (unsigned)(A_of(-da) + RB_of(-db) + cs * NAB);
+  };
+
+  // FP32 storage: the incoming g of plane cg (own cell and this thread's
+  // halo cells) and the own cell's f of plane cf are copied asynchronously
+  // into this thread's slots of stage s a plane before they are used. Each
+  // thread reads back only its own slots, so completing its own copies
+  // (cp.async.wait_group) is all the synchronisation needed.
+  auto stage_f = [&](int s) { return s_stage + s * (FST + GST); };
+  auto stage_g = [&](int s) { return s_stage + s * (FST + GST) + FST; };
+  auto issue = [&](int cg, int cf, int s) {
+    const float* gs32 = reinterpret_cast<const float*>(gsrc);
+    const float* fb32 = reinterpret_cast<const float*>(fb);
+    float* gs = stage_g(s);
+    const unsigned pofs = (unsigned)(NAB * map_c(cg));
+#pragma unroll
+    for (int q = SKIP0 ? 1 : 0; q < QG; ++q) cp_async4(gs + q * PLANE + tid, gs32 + (q * N + own_ab + pofs));
+#pragma unroll
+    for (int k = 0; k < KH; ++k) {
+      if (halo_pos[k] >= 0) {
+#pragma unroll
+        for (int q = SKIP0 ? 1 : 0; q < QG; ++q)
+          cp_async4(gs + q * PLANE + NT + tid + k * NT, gs32 + (q * N + halo_ab[k] + pofs));
+      }
+    }
+    if (active) {
+      float* fs = stage_f(s);
+#pragma unroll
+      for (int q = 0; q < QF; ++q) cp_async4(fs + q * NT + tid, fb32 + f_read_ofs(cf, q));
+    }
+  };
+  // phi of logical plane c from stage s into the ring; keeps the own cell's g.
+  auto produce_staged = [&](int c, int s, float (&gown)[QG]) {
+    const float* gs = stage_g(s);
+    float* slot = ring(c);
+#pragma unroll
+    for (int q = 0; q < QG; ++q) gown[q] = (SKIP0 && q == 0) ? 0.0f : gs[q * PLANE + tid];
+    slot[own_slot] = finish_phi<FAM>(P, phi_star<LG, SKIP0>(gown), gamma);
+#pragma unroll
+    for (int k = 0; k < KH; ++k) {
+      if (halo_pos[k] >= 0) {
+        float tmp[QG];
+#pragma unroll
+        for (int q = 0; q < QG; ++q) tmp[q] = (SKIP0 && q == 0) ? 0.0f : gs[q * PLANE + NT + tid + k * NT];
+        slot[halo_pos[k]] = finish_phi<FAM>(P, phi_star<LG, SKIP0>(tmp), gamma);
+      }
+    }
+  };
+
   float g0[QG], g1[QG], g2[QG];
   // Prologue: planes c0-H .. c0+H-1.
   {
@@ -490,28 +572,30 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
     produce(c0, g0);
     if constexpr (CH) produce(c0 + 1, g1);
   }
+  if constexpr (STAGED) {
+    issue(c0 + H, c0, 0);
+    cp_async_commit();
+    if (c0 + 1 < c1) issue(c0 + 1 + H, c0 + 1, 1);
+    cp_async_commit();
+  }
   if constexpr (CH) {
     __syncthreads();
     make_mu(c0 - 1);
     make_mu(c0);
   }
 
-  // Own-cell neighbour coordinates along the fast axes (constant).
-  const int aw = (a < NA) ? a : 0, bw = (b < NB) ? b : 0;
-  const int am = aw == 0 ? NA - 1 : aw - 1, ap = aw == NA - 1 ? 0 : aw + 1;
-  const int bm = bw == 0 ? NB - 1 : bw - 1, bp = bw == NB - 1 ? 0 : bw + 1;
-  const int rbm = bm * NA, rbw = bw * NA, rbp = bp * NA;
-  auto A_of = [&](int d) { return d < 0 ? am : (d > 0 ? ap : aw); };
-  auto RB_of = [&](int d) { return d < 0 ? rbm : (d > 0 ? rbp : rbw); };
-
   for (int c = c0; c < c1; ++c) {
+    const int st = (c - c0) & 1;
+    if constexpr (STAGED) cp_async_wait<1>();   // stage st (plane c) has landed; c + 1 may be in flight
     if constexpr (CH) {
-      produce(c + 2, g2);
+      if constexpr (STAGED) produce_staged(c + 2, st, g2);
+      else produce(c + 2, g2);
       __syncthreads();
       make_mu(c + 1);
       __syncthreads();
     } else {
-      produce(c + 1, g1);
+      if constexpr (STAGED) produce_staged(c + 1, st, g1);
+      else produce(c + 1, g1);
       __syncthreads();
     }
 
@@ -562,14 +646,13 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
 
       // Pre-collision f (AA pattern).
       float f[QF];
+      if constexpr (STAGED) {
+        const float* fs = stage_f(st);
 #pragma unroll
-      for (int q = 0; q < QF; ++q) {
-        const int da = da_of<DIM, LF>(q), db = db_of<DIM, LF>(q), dc = dc_of<DIM, LF>(q);
-        if (args.parity == 0 || crosses(-dc)) {
-          f[q] = pop_loadc<T, LF>(fb + (q * N + idx), q, 0.0f);
-        } else {
-          f[q] = pop_loadc<T, LF>(fb + (LF::opp(q) * N + nidx(-da, -db, -dc)), q, 0.0f);
-        }
+        for (int q = 0; q < QF; ++q) f[q] = fs[q * NT + tid];
+      } else {
+#pragma unroll
+        for (int q = 0; q < QF; ++q) f[q] = pop_loadc<T, LF>(fb + f_read_ofs(c, q), q, 0.0f);
       }
       float phiu[DIM];
       if constexpr (CH) {
@@ -648,6 +731,13 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
       }
     }
 
+    // Refill the stage just consumed with plane c + 2 (issued here, where
+    // the fewest values are live).
+    if constexpr (STAGED) {
+      if (c + 2 < c1) issue(c + 2 + H, c + 2, st);
+      cp_async_commit();
+    }
+
     // Rotate the own-cell g pipeline.
 #pragma unroll
     for (int q = 0; q < QG; ++q) {
@@ -662,12 +752,14 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
 // The single-domain kernel: one tile per block.
 // ---------------------------------------------------------------------------
 template <int FAM, int DIM, typename T>
-__global__ void __launch_bounds__(Geom<DIM>::TA * Geom<DIM>::TB, Geom<DIM>::MINB)
+__global__ void __launch_bounds__(Geom<FAM, DIM, T>::TA * Geom<FAM, DIM, T>::TB, Geom<FAM, DIM, T>::MINB)
 step_kernel(const StepArgs args) {
-  constexpr int TA = Geom<DIM>::TA, TB = Geom<DIM>::TB;
-  using SM = TileSmem<FAM, DIM, TA, TB>;
-  __shared__ float s_phi[SM::PHI];
-  __shared__ float s_mu[SM::MU];
+  constexpr int TA = Geom<FAM, DIM, T>::TA, TB = Geom<FAM, DIM, T>::TB;
+  using SM = TileSmem<FAM, DIM, T, TA, TB>;
+  extern __shared__ __align__(16) float dyn_smem[];
+  float* s_stage = dyn_smem;
+  float* s_phi = dyn_smem + SM::STAGE;
+  float* s_mu = s_phi + SM::PHI;
   __shared__ double s_red[(TA * TB / 32) * 10];
   const int NA = args.p.nx, NB = (DIM == 3) ? args.p.ny : 1;
   const int tiles_a = (NA + TA - 1) / TA, tiles_b = (NB + TB - 1) / TB;
@@ -680,18 +772,22 @@ step_kernel(const StepArgs args) {
     obs_zero_slot(args.obs_zero);
   ObsPartial obs;
   obs_init(obs);
-  step_tile<FAM, DIM, T, TA, TB>(args, ti * TA, tj * TB, bid * args.chunk, args.chunk, s_phi, s_mu, obs);
+  step_tile<FAM, DIM, T, TA, TB>(args, ti * TA, tj * TB, bid * args.chunk, args.chunk, s_phi, s_mu, s_stage, obs);
   obs_block_commit(obs, args.obs_slot, s_red);
 }
 
 template <int FAM, int DIM, typename T>
 void launch_step(const StepArgs& args, cudaStream_t stream) {
-  constexpr int TA = Geom<DIM>::TA, TB = Geom<DIM>::TB;
+  constexpr int TA = Geom<FAM, DIM, T>::TA, TB = Geom<FAM, DIM, T>::TB;
+  constexpr size_t smem = TileSmem<FAM, DIM, T, TA, TB>::BYTES;
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      step_kernel<FAM, DIM, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  (void)attr;
   const int NA = args.p.nx, NB = (DIM == 3) ? args.p.ny : 1, NC = (DIM == 3) ? args.p.nz : args.p.ny;
   const long long tiles = (long long)((NA + TA - 1) / TA) * ((NB + TB - 1) / TB);
   const long long chunks = (NC + args.chunk - 1) / args.chunk;
   dim3 block(TA, TB, 1);
-  step_kernel<FAM, DIM, T><<<(unsigned)(tiles * chunks), block, 0, stream>>>(args);
+  step_kernel<FAM, DIM, T><<<(unsigned)(tiles * chunks), block, smem, stream>>>(args);
 }
 
 }  // namespace pflb
