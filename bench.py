@@ -15,7 +15,9 @@ W = 4, We = 5, density ratio 1, linear forcing, conservative Allen-Cahn
   variants     FP16 / BF16 deviation storage of the same workload, and the
                batched form: 512 2D droplet-in-shear domains (sizes uniform in
                {64,128,256,512}^2, the four families mixed) in one persistent
-               launch per step, autotuned launch shape, CUDA-graph replay
+               launch per step, autotuned launch shape, CUDA-graph replay;
+               and the adjoint (forward + reverse sweep) of the 128^3
+               droplet-in-Taylor-Green case over 2000 steps
   cpu_baseline the FP64 oracle on a bounded sample, host cores
 
 --impl reference times the FP64 oracle (the only reference this method has)
@@ -223,6 +225,51 @@ def batched_variant(steps, warmup, peak, count=512):
                              "sampled domains vs FP64 oracle as the 2D fp32 path (tests/test_gpu_batch.py)"}
 
 
+def adjoint_variant(n=128, nsteps=2000):
+    """Adjoint of the 3D droplet in a Taylor-Green vortex (n^3 periodic, R = 24,
+    W = 4, u0 = 0.02, M = 0.1, sigma = 1e-3, tau = 0.8): forward sweep with
+    ceil(sqrt(nsteps)) checkpoints, recomputation and reverse sweep of
+    nsteps steps; J = V_s + c_z. Also the central difference of the FP32
+    forward runs for dJ/dsigma (h = 1e-2 sigma) as a check."""
+    import numpy as np
+    import torch
+    from paper_2511_11360_gb300 import cases as C
+    from paper_2511_11360_gb300 import pflb
+    P, phi, u = C.droplet_in_tgv_3d(n=n, R=24.0, W=4.0, u0=0.02)
+    phi = np.asarray(phi, np.float32)
+    u = np.asarray(u, np.float32)
+    stream = torch.cuda.current_stream()
+    w = dict(w_vol=1.0, w_cen=(0.0, 0.0, 1.0), eps_v=0.05)
+    s = pflb.Sim(dict(P, storage=0), stream=stream)
+    s.init(phi, u)
+    du0 = torch.zeros((3, n, n, n), device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = s.adjoint(nsteps, du0=du0, **w)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    s.close()
+
+    def J_of(sig):
+        sm = pflb.Sim(dict(P, storage=0, sigma=sig), stream=stream)
+        sm.init(phi, u)
+        sm.step(nsteps)
+        ph = torch.empty((n, n, n), device="cuda")
+        sm.fields(phi=ph)
+        sm.close()
+        ph = ph.double()
+        z = torch.arange(n, device="cuda", dtype=torch.float64).reshape(n, 1, 1)
+        return float((0.5 * (1.0 + torch.tanh((ph - 0.5) / w["eps_v"]))).sum() + (z * ph).sum() / ph.sum())
+
+    h = 1e-2 * P["sigma"]
+    fd = (J_of(P["sigma"] + h) - J_of(P["sigma"] - h)) / (2 * h)
+    return {"workload": "3D droplet in Taylor-Green vortex %d^3 periodic, R=24, W=4, u0=0.02, Fakhari2017 FP32" % n,
+            "steps": nsteps, "seconds": t, "forward_plus_reverse_GLUPS": n ** 3 * nsteps / t / 1e9,
+            "checkpoint_every": g["checkpoint_every"], "checkpoints": g["checkpoints"],
+            "J": g["J"], "dJ_dM": g["dJ_dM"], "dJ_dsigma": g["dJ_dsigma"], "dJ_dW": g["dJ_dW"],
+            "dJ_dsigma_central_difference_fp32": fd, "max_abs_dJ_du0": float(du0.abs().max())}
+
+
 def cpu_baseline(seconds_target=15.0):
     """The FP64 oracle, unmodified, on a bounded sample of the workload: a
     periodic 64^3 box of the same recipe (2 droplets of R = 16, W = 4,
@@ -289,6 +336,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -360,6 +408,8 @@ def main():
 
         if not args.no_batched:
             variants["batched_2d_shear_512"] = batched_variant(args.steps, args.warmup, peak)
+        if not args.no_adjoint:
+            variants["adjoint_tgv_128"] = adjoint_variant()
 
     # ---- end to end through the C ABI with host buffers
     phi_h = torch.empty(phi.shape, dtype=torch.float32, pin_memory=True)

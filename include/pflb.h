@@ -190,6 +190,66 @@ int pflb_destroy(pflb_handle* h);
 const char* pflb_last_error(const pflb_handle* h);
 
 /* ---------------------------------------------------------------------------
+ * Adjoint: gradients of a droplet objective by a reverse sweep.
+ *
+ * For the conservative Allen-Cahn family (Fakhari2017, Sec. II C 1) on a
+ * periodic domain at density ratio 1 (rho_H = rho_L; the viscosities may
+ * differ, linear interpolation), FP32 storage, 2D or 3D, pflb_adjoint runs
+ * nsteps time levels from the state pflb_init made and returns the
+ * objective of the final state
+ *     J = w_vol V_s + sum_k w_cen[k] c_k,
+ *     V_s = sum_x (1 + tanh((phi - phi_0)/eps_v))/2   (smooth volume),
+ *     c_k = sum_x x_k phi / sum_x phi                 (centroid, cell-index
+ *                                                      coordinates)
+ * with phi = sum_a g_a of the final state, and its derivatives with respect
+ * to the mobility M, the surface tension sigma, the interface width W and
+ * the initial velocity field u0 given to pflb_init (through the
+ * equilibrium initial populations). The reverse sweep differentiates the
+ * step exactly as the library computes it (stencils of Sec. III,
+ * regularised normal of the counter term), in FP32 with FP64 parameter sums.
+ *
+ * Checkpointing: the forward sweep keeps every checkpoint_every-th state
+ * (0 = ceil(sqrt(nsteps))); the reverse sweep recomputes each segment from
+ * its checkpoint and walks it backwards. Device memory: (nsteps/K + K + 3)
+ * canonical states (pflb_state_floats floats each) plus small buffers,
+ * allocated for the call and freed before it returns.
+ *
+ * The handle must be initialised and at step 0; on success it is left at
+ * step nsteps with the state and observables records pflb_step(h, nsteps)
+ * gives. du0: NULL or d*N floats (host or device, layout of the u0 given to
+ * pflb_init) that receive dJ/du0. Synchronises the stream.
+ *
+ * Errors: PFLB_EINVAL for another family, walls, 16-bit storage, a density
+ * contrast, a non-linear viscosity interpolation, freeze_phi, a handle not at
+ * step 0, nsteps < 1 or eps_v <= 0; PFLB_ENOMEM when the checkpoints do not
+ * fit; PFLB_EUNSTABLE when the final sum of phi is zero or not finite.
+ *
+ * Conditioning: where the counter term of Eq. (fakhari_G_modified) acts on
+ * a droplet whose centre is not saturated (R/W below about 2.5 at
+ * grad_eps = 1e-4), its regularised normal is anti-diffusive there and the
+ * model amplifies perturbations; gradients are then dominated by that
+ * amplification (finite differences of such runs are noise).
+ * ------------------------------------------------------------------------- */
+typedef struct pflb_obs_weights {
+  double w_vol;     /* weight of V_s */
+  double w_cen[3];  /* weights of the centroid components (x, y, z; z unused in 2D) */
+  double eps_v;     /* width of the smooth volume indicator, > 0 (e.g. 0.05) */
+} pflb_obs_weights;
+
+typedef struct pflb_grads {
+  double J;                          /* objective of the final state */
+  double vol_smooth;                 /* V_s of the final state */
+  double centroid[3];                /* c_k of the final state */
+  double dJ_dM, dJ_dsigma, dJ_dW;    /* parameter derivatives */
+  int64_t steps;
+  int32_t checkpoint_every;          /* K used */
+  int32_t checkpoints;               /* states kept by the forward sweep */
+} pflb_grads;
+
+int pflb_adjoint(pflb_handle* h, int64_t nsteps, int32_t checkpoint_every, const pflb_obs_weights* w,
+                 pflb_grads* out, float* du0);
+
+/* ---------------------------------------------------------------------------
  * Batched step: many independent 2D domains in one persistent launch.
  *
  * A batch owns n domains (pflb_handle each) of any size, family and

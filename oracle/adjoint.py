@@ -43,16 +43,16 @@ DEFAULT_WEIGHTS = dict(w_vol=1.0, w_cen=(0.0, 0.0, 0.0), eps_v=0.05)
 
 
 class TorchLattice:
-    def __init__(self, lat):
+    def __init__(self, lat, dtype=torch.float64):
         self.Q, self.d = lat.Q, lat.d
         self.e = [tuple(int(v) for v in lat.e[a]) for a in range(lat.Q)]
-        self.ef = torch.tensor(lat.ef, dtype=torch.float64)
-        self.w = torch.tensor(lat.w, dtype=torch.float64)
+        self.ef = torch.tensor(lat.ef, dtype=dtype)
+        self.w = torch.tensor(lat.w, dtype=dtype)
         self.cs2 = lat.cs2
 
 
-def lattices(dim):
-    return tuple(TorchLattice(l) for l in O.lattices_for(dim))
+def lattices(dim, dtype=torch.float64):
+    return tuple(TorchLattice(l, dtype) for l in O.lattices_for(dim))
 
 
 def _shifted(field, e):
@@ -128,7 +128,7 @@ def _check_scope(P):
 
 def init(P, phi0, u0):
     """Equilibrium populations with p = 0 (Reading R8), differentiable in u0."""
-    lg, lf, _ = lattices(P["dim"])
+    lg, lf, _ = lattices(P["dim"], phi0.dtype)
     g = _geq(lg, phi0, u0)
     f = _feq(lf, torch.zeros_like(phi0), u0)
     return g, f
@@ -136,7 +136,7 @@ def init(P, phi0, u0):
 
 def step(P, g, f, M, sigma, W):
     """One coupled step (macroscopic stage, both collisions, push streaming)."""
-    lg, lf, ls = lattices(P["dim"])
+    lg, lf, ls = lattices(P["dim"], g.dtype)
     phiH, phiL = P["phi_H"], P["phi_L"]
     dphi = phiH - phiL
     phi0 = 0.5 * (phiH + phiL)
@@ -156,8 +156,8 @@ def step(P, g, f, M, sigma, W):
     grho = drho * gp
     mu = 4.0 * beta * (phi - phiH) * (phi - phiL) * (phi - phi0) - kappa * lp
     d = P["dim"]
-    gvec = torch.tensor(list(P["gravity"])[:d], dtype=torch.float64).reshape((-1,) + (1,) * phi.ndim)
-    fvec = torch.tensor(list(P["force_density"])[:d], dtype=torch.float64).reshape((-1,) + (1,) * phi.ndim)
+    gvec = torch.tensor(list(P["gravity"])[:d], dtype=g.dtype).reshape((-1,) + (1,) * phi.ndim)
+    fvec = torch.tensor(list(P["force_density"])[:d], dtype=g.dtype).reshape((-1,) + (1,) * phi.ndim)
     Fs = mu * gp
     Fb = rho * gvec + fvec
     A = P["lundgren_A"]
@@ -201,7 +201,7 @@ def objective(P, g, weights=None):
             ax = d - 1 - k
             shape = [1] * d
             shape[ax] = phi.shape[ax]
-            xk = torch.arange(phi.shape[ax], dtype=torch.float64).reshape(shape)
+            xk = torch.arange(phi.shape[ax], dtype=phi.dtype).reshape(shape)
             J = J + wt["w_cen"][k] * (xk * phi).sum() / S
     return J
 
@@ -217,17 +217,19 @@ def run_objective(P, phi0, u0, nsteps, M, sigma, W, weights=None, checkpoint=Tru
     return objective(P, g, weights)
 
 
-def reverse_sweep(P, phi0, u0, nsteps, weights=None):
+def reverse_sweep(P, phi0, u0, nsteps, weights=None, dtype=torch.float64):
     """J and its gradient with respect to M, sigma, W and u0 (reverse mode).
     phi0 (field) and u0 (d, field) are numpy arrays; returns a dict of floats
-    and the (d, field) array dJ/du0."""
+    and the (d, field) array dJ/du0. dtype float32 evaluates the same
+    equations in single precision (to size the FP32 floor of a gradient)."""
     _check_scope(P)
-    th = {k: torch.tensor(float(P[k]), dtype=torch.float64, requires_grad=True) for k in ("M", "sigma", "W")}
-    phi = torch.tensor(np.asarray(phi0, dtype=np.float64))
-    u = torch.tensor(np.asarray(u0, dtype=np.float64), requires_grad=True)
+    th = {k: torch.tensor(float(P[k]), dtype=dtype, requires_grad=True) for k in ("M", "sigma", "W")}
+    phi = torch.tensor(np.asarray(phi0), dtype=dtype)
+    u = torch.tensor(np.asarray(u0), dtype=dtype, requires_grad=True)
     J = run_objective(P, phi, u, nsteps, th["M"], th["sigma"], th["W"], weights)
     gM, gs, gW, gu = torch.autograd.grad(J, [th["M"], th["sigma"], th["W"], u])
-    return dict(J=float(J.detach()), dM=float(gM), dsigma=float(gs), dW=float(gW), du0=gu.numpy())
+    return dict(J=float(J.detach()), dM=float(gM), dsigma=float(gs), dW=float(gW),
+                du0=gu.numpy().astype(np.float64))
 
 
 def directional_derivative(P, phi0, u0, v, nsteps, weights=None):

@@ -242,6 +242,22 @@ int macro_pass(pflb_handle* h, float* phi, float* u, float* p) {
 
 }  // namespace
 
+int pflb::handle_canon(pflb_handle* h, float* state_dev, int to_canon) {
+  CanonArgs a;
+  a.p = h->dp;
+  a.g = h->g[h->cur];
+  a.f = h->f;
+  a.phiu = h->phiu;
+  a.state = state_dev;
+  a.parity = (int)(h->step & 1);
+  a.to_canon = to_canon;
+  a.ch = h->family == 3;
+  a.N = h->N;
+  canon_copy(h->dim, h->storage, a, h->stream);
+  CU(h, cudaGetLastError());
+  return PFLB_OK;
+}
+
 extern "C" {
 
 int pflb_create(const pflb_params* params, void* cuda_stream, pflb_handle** out) {
@@ -424,32 +440,17 @@ int64_t pflb_state_floats(const pflb_handle* h) {
   return (int64_t)(h->QG + h->QF + (h->family == 3 ? h->dim : 0)) * h->N;
 }
 
-static int canon(pflb_handle* h, float* state_dev, int to_canon) {
-  CanonArgs a;
-  a.p = h->dp;
-  a.g = h->g[h->cur];
-  a.f = h->f;
-  a.phiu = h->phiu;
-  a.state = state_dev;
-  a.parity = (int)(h->step & 1);
-  a.to_canon = to_canon;
-  a.ch = h->family == 3;
-  a.N = h->N;
-  canon_copy(h->dim, h->storage, a, h->stream);
-  CU(h, cudaGetLastError());
-  return PFLB_OK;
-}
 
 int pflb_save(pflb_handle* h, float* state) {
   if (!h || !state) return handle_fail(h, PFLB_EINVAL, "null argument");
   const size_t nb = (size_t)pflb_state_floats(h) * sizeof(float);
   if (is_device_ptr(state)) {
-    int rc = canon(h, state, 1);
+    int rc = handle_canon(h, state, 1);
     if (rc) return rc;
   } else {
     float* tmp = nullptr;
     CU(h, cudaMalloc(&tmp, nb));
-    int rc = canon(h, tmp, 1);
+    int rc = handle_canon(h, tmp, 1);
     if (rc == PFLB_OK) {
       cudaError_t e = cudaMemcpyAsync(state, tmp, nb, cudaMemcpyDeviceToHost, h->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -476,7 +477,7 @@ int pflb_load(pflb_handle* h, const float* state) {
     }
     src = tmp;
   }
-  int rc = canon(h, src, 0);
+  int rc = handle_canon(h, src, 0);
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (tmp) cudaFree(tmp);
   if (rc) return rc;

@@ -34,6 +34,9 @@ int num_sms();
 bool handle_nonlocal(const pflb_handle* h);
 // Launch arguments of the next step of h (no observables slots set).
 StepArgs handle_step_args(const pflb_handle* h);
+// Copy between the handle's storage and a canonical FP32 state in device
+// memory (to_canon = 1: storage -> state), asynchronously on its stream.
+int handle_canon(pflb_handle* h, float* state_dev, int to_canon);
 // Host form of a device observables record.
 void obs_to_host(const DevObs& d, long long step, pflb_obs* o);
 // Records a message and a sticky status on h; returns code.

@@ -52,6 +52,21 @@ class BatchLaunch(ctypes.Structure):
                     from_cache=self.from_cache, ms_per_step=self.ms_per_step)
 
 
+class ObsWeights(ctypes.Structure):
+    _fields_ = [("w_vol", ctypes.c_double), ("w_cen", ctypes.c_double * 3), ("eps_v", ctypes.c_double)]
+
+
+class Grads(ctypes.Structure):
+    _fields_ = [("J", ctypes.c_double), ("vol_smooth", ctypes.c_double), ("centroid", ctypes.c_double * 3),
+                ("dJ_dM", ctypes.c_double), ("dJ_dsigma", ctypes.c_double), ("dJ_dW", ctypes.c_double),
+                ("steps", ctypes.c_int64), ("checkpoint_every", ctypes.c_int32), ("checkpoints", ctypes.c_int32)]
+
+    def to_dict(self):
+        return dict(J=self.J, vol_smooth=self.vol_smooth, centroid=list(self.centroid), dJ_dM=self.dJ_dM,
+                    dJ_dsigma=self.dJ_dsigma, dJ_dW=self.dJ_dW, steps=self.steps,
+                    checkpoint_every=self.checkpoint_every, checkpoints=self.checkpoints)
+
+
 class Obs(ctypes.Structure):
     _fields_ = [
         ("step", ctypes.c_int64), ("sum_phi", ctypes.c_double), ("vol_smooth", ctypes.c_double),
@@ -90,6 +105,8 @@ SIGNATURES = {
     "pflb_phase_sums_static": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_void_p, ctypes.POINTER(Obs),
                                               ctypes.c_void_p]),
     "pflb_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "pflb_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ObsWeights),
+                                    ctypes.POINTER(Grads), ctypes.c_void_p]),
     "pflb_batch_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int32, ctypes.c_void_p,
                                          ctypes.POINTER(ctypes.c_void_p)]),
     "pflb_batch_size": (ctypes.c_int32, [ctypes.c_void_p]),
@@ -283,6 +300,16 @@ class Sim:
         if isinstance(state, np.ndarray):
             state = np.ascontiguousarray(state, dtype=np.float32)
         return self._check(self.lib.pflb_load(self.h, _ptr(state)))
+
+    def adjoint(self, nsteps, w_vol=1.0, w_cen=(0.0, 0.0, 0.0), eps_v=0.05, du0=None, checkpoint_every=0):
+        """pflb_adjoint: run nsteps from the initial state and return J and its
+        derivatives (dict); dJ/du0 goes into du0 (host array or device
+        tensor of the u0 layout) when given."""
+        w = ObsWeights(float(w_vol), (ctypes.c_double * 3)(*[float(v) for v in w_cen]), float(eps_v))
+        g = Grads()
+        self._check(self.lib.pflb_adjoint(self.h, int(nsteps), int(checkpoint_every), ctypes.byref(w),
+                                          ctypes.byref(g), _ptr(du0)))
+        return g.to_dict()
 
 
 class Batch:
