@@ -40,7 +40,31 @@ sys.path.insert(0, ROOT)
 WORKLOAD = ("3D droplet-laden forced HIT 512^3 periodic, D3Q19+D3Q7, 200 droplets R=16, W=4, "
             "We=5, density ratio 1, linear forcing, conservative Allen-Cahn (Fakhari2017)")
 METRIC = "coupled GLUPS (512^3 D3Q19+D3Q7 fused PF-LB step)"
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "step_kernel_traffic_fakhari3d_fp32.txt")
+KERNEL_SOURCES = ["pflb_step.cuh", "pflb_common.cuh", "pflb_symsum.cuh", "pflb_args.h", "pflb_fam_fakhari.cu"]
+
+
+def _traffic(n):
+    """DRAM bytes per launch of the FP32 step from the committed ncu record,
+    or None when the record is for another size or the kernel sources have
+    changed since the counters were taken (sha256 of the sources)."""
+    import hashlib
+    try:
+        rec = {}
+        with open(PROFILE_TRAFFIC) as fh:
+            for line in fh:
+                if "=" in line and not line.lstrip().startswith("#"):
+                    k, v = line.split("=", 1)
+                    rec[k.strip()] = v.strip()
+        h = hashlib.sha256()
+        for f in KERNEL_SOURCES:
+            with open(os.path.join(ROOT, "paper_2511_11360_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+        if int(rec["workload_n"]) == n and rec["source_sha256"] == h.hexdigest():
+            return float(rec["bytes_per_launch"])
+    except Exception:
+        pass
+    return None
 
 
 def _peaks():
@@ -382,14 +406,7 @@ def main():
     value = cells * args.steps * world / t / 1e9
     ms = t / args.steps * 1e3
     achieved = bytes_lu * cells / (t / args.steps) / 1e9
-    traffic = None
-    try:
-        with open(PROFILE_TRAFFIC) as fh:
-            tr = json.load(fh)
-        if tr.get("workload_n") == n and tr.get("kernel_rev") == "v1":
-            traffic = tr.get("bytes_per_launch")
-    except Exception:
-        pass
+    traffic = _traffic(n) if storage == 0 else None
 
     # ---- variants: FP16 / BF16 deviation storage
     variants = {}
