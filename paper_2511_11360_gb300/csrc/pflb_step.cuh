@@ -287,12 +287,19 @@ struct Cell {
         f[q] = f[q] - (f[q] - feq) * itau + fw * Fq;
       }
     } else {
+      // f* = f - (f - f_eq) itau + fw F_b = f (1 - itau) + w (itau X + fw Y), with
+      // f_eq = w X, X = sum f + 3 e.u + 4.5 (e.u)^2 - 1.5 u.u   Eq. (fakhari_feq),
+      // F_b = w Y, Y = 3 e.F~ (Eq. fakhari_F) or
+      //       3 e.F~ + 9 (e.u)(e.F~) - 3 u.F~ (Eq. chai_F, Reading R2), F~ = F/rho;
+      // one weight product per velocity.
       float Ft[DIM], uFt = 0.0f;
 #pragma unroll
       for (int k = 0; k < DIM; ++k) {
         Ft[k] = F[k] * inv_rho;
         uFt += u[k] * Ft[k];
       }
+      const float s0 = sumf - 1.5f * usq;
+      const float omi = 1.0f - itau;
 #pragma unroll
       for (int q = 0; q < QF; ++q) {
         float eu = 0.0f, eF = 0.0f;
@@ -303,11 +310,11 @@ struct Cell {
             eu += e * u[k];
             eF += e * Ft[k];
           }
-        const float feq = wmul<LF>(q, sumf + 3.0f * eu + 4.5f * eu * eu - 1.5f * usq);  // Eq. (fakhari_feq)
-        float Fq;
-        if constexpr (FAM == FAM_FAKHARI) Fq = wmul<LF>(q, 3.0f * eF);                     // Eq. (fakhari_F)
-        else Fq = wmul<LF>(q, 3.0f * eF + 9.0f * eu * eF - 3.0f * uFt);                   // Eq. (chai_F), Reading R2
-        f[q] = f[q] - (f[q] - feq) * itau + fw * Fq;
+        const float X = fmaf(eu, fmaf(4.5f, eu, 3.0f), s0);
+        float Y;
+        if constexpr (FAM == FAM_FAKHARI) Y = 3.0f * eF;
+        else Y = fmaf(9.0f * eu, eF, 3.0f * (eF - uFt));
+        f[q] = fmaf(f[q], omi, wmul<LF>(q, fmaf(itau, X, fw * Y)));
       }
     }
   }
@@ -341,7 +348,7 @@ struct TileSmem {
 // kernel (one tile per block) and by the persistent batch kernel (tiles of
 // many domains claimed in turn). Accumulates the observables into obs.
 // ---------------------------------------------------------------------------
-template <int FAM, int DIM, typename T, int TA, int TB>
+template <int FAM, int DIM, typename T, int TA, int TB, int PAR = -1>
 __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, int c0, int chunk,
                                           float* __restrict__ s_phi, float* __restrict__ s_mu,
                                           float* __restrict__ s_stage, ObsPartial& obs) {
@@ -379,6 +386,9 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
   const int a = a0 + tx, b = b0 + ty;
   const bool active = (a < NA) && (b < NB);
   const bool walls = P.walls != 0;
+  // AA parity of this step: a compile-time constant for the single-domain
+  // kernel (one instantiation per parity), read from the arguments otherwise.
+  const int parity = PAR >= 0 ? PAR : args.parity;
 
   float gamma = 0.0f;
   if constexpr (FAM == FAM_CHAI || FAM == FAM_HU) {
@@ -512,7 +522,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
   auto f_read_ofs = [&](int c, int q) -> unsigned {
     const int da = da_of<DIM, LF>(q), db = db_of<DIM, LF>(q), dc = dc_of<DIM, LF>(q);
     const bool cross = walls && ((dc > 0 && c == 0) || (dc < 0 && c == NC - 1));
-    if (args.parity == 0 || cross) return q * N + (unsigned)(aw + rbw + c * NAB);
+    if (parity == 0 || cross) return q * N + (unsigned)(aw + rbw + c * NAB);
     const int cs = dc > 0 ? (c == 0 ? NC - 1 : c - 1) : (dc < 0 ? (c == NC - 1 ? 0 : c + 1) : c);
     return LF::opp(q) * N + (unsigned)(A_of(-da) + RB_of(-db) + cs * NAB);
   };
@@ -676,9 +686,10 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
         for (int k = 0; k < DIM; ++k) usq += u[k] * u[k];
         obs.vs += fr;
         obs.ke += 0.5f * rho * usq;
-        obs.cx += (float)aw * fr;
-        obs.cy += (float)(DIM == 3 ? bw : c) * fr;
-        obs.cz += (float)(DIM == 3 ? c : 0) * fr;
+        // The fast-axis coordinates are fixed per thread: their moments are
+        // aw (and bw in 3D) times the thread's volume sum, formed at the end.
+        if constexpr (DIM == 3) obs.cz += (float)c * fr;
+        else obs.cy += (float)c * fr;
         obs.count += (pc > P.phi0) ? 1u : 0u;
         obs.mx = fmaxf(obs.mx, pc);
         obs.mn = fminf(obs.mn, pc);
@@ -722,7 +733,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
             const float uw = dc < 0 ? uw_lo : uw_hi;
             v -= 6.0f * LF::w(q) * sc * (float)LF::ex(q) * uw;
           }
-          if (args.parity == 0 || cr) {
+          if (parity == 0 || cr) {
             pop_store<T, LF>(fb + (LF::opp(q) * N + idx), q, v, 0.0f);
           } else {
             pop_store<T, LF>(fb + (q * N + nidx(da, db, dc)), q, v, 0.0f);
@@ -746,12 +757,16 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
     }
   }
 
+  // Centroid moments along the fast axes, whose coordinates are fixed per
+  // thread (inactive threads added nothing to vs).
+  obs.cx += (float)aw * obs.vs;
+  if constexpr (DIM == 3) obs.cy += (float)bw * obs.vs;
 }
 
 // ---------------------------------------------------------------------------
 // The single-domain kernel: one tile per block.
 // ---------------------------------------------------------------------------
-template <int FAM, int DIM, typename T>
+template <int FAM, int DIM, typename T, int PAR>
 __global__ void __launch_bounds__(Geom<FAM, DIM, T>::TA * Geom<FAM, DIM, T>::TB, Geom<FAM, DIM, T>::MINB)
 step_kernel(const StepArgs args) {
   constexpr int TA = Geom<FAM, DIM, T>::TA, TB = Geom<FAM, DIM, T>::TB;
@@ -772,22 +787,29 @@ step_kernel(const StepArgs args) {
     obs_zero_slot(args.obs_zero);
   ObsPartial obs;
   obs_init(obs);
-  step_tile<FAM, DIM, T, TA, TB>(args, ti * TA, tj * TB, bid * args.chunk, args.chunk, s_phi, s_mu, s_stage, obs);
+  step_tile<FAM, DIM, T, TA, TB, PAR>(args, ti * TA, tj * TB, bid * args.chunk, args.chunk, s_phi, s_mu, s_stage,
+                                      obs);
   obs_block_commit(obs, args.obs_slot, s_red);
 }
 
-template <int FAM, int DIM, typename T>
-void launch_step(const StepArgs& args, cudaStream_t stream) {
+template <int FAM, int DIM, typename T, int PAR>
+void launch_step_par(const StepArgs& args, cudaStream_t stream) {
   constexpr int TA = Geom<FAM, DIM, T>::TA, TB = Geom<FAM, DIM, T>::TB;
   constexpr size_t smem = TileSmem<FAM, DIM, T, TA, TB>::BYTES;
   static const cudaError_t attr = cudaFuncSetAttribute(
-      step_kernel<FAM, DIM, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      step_kernel<FAM, DIM, T, PAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   (void)attr;
   const int NA = args.p.nx, NB = (DIM == 3) ? args.p.ny : 1, NC = (DIM == 3) ? args.p.nz : args.p.ny;
   const long long tiles = (long long)((NA + TA - 1) / TA) * ((NB + TB - 1) / TB);
   const long long chunks = (NC + args.chunk - 1) / args.chunk;
   dim3 block(TA, TB, 1);
-  step_kernel<FAM, DIM, T><<<(unsigned)(tiles * chunks), block, smem, stream>>>(args);
+  step_kernel<FAM, DIM, T, PAR><<<(unsigned)(tiles * chunks), block, smem, stream>>>(args);
+}
+
+template <int FAM, int DIM, typename T>
+void launch_step(const StepArgs& args, cudaStream_t stream) {
+  if (args.parity) launch_step_par<FAM, DIM, T, 1>(args, stream);
+  else launch_step_par<FAM, DIM, T, 0>(args, stream);
 }
 
 }  // namespace pflb
