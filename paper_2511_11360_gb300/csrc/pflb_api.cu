@@ -65,9 +65,11 @@ int validate(const pflb_params* p, char* msg, size_t n) {
   if (p->nx < 1 || p->ny < 1 || p->nz < 1) return snprintf(msg, n, "sizes must be >= 1"), PFLB_EINVAL;
   if (p->dim == 2 && p->nz != 1) return snprintf(msg, n, "nz must be 1 in 2D"), PFLB_EINVAL;
   const long long N = (long long)p->nx * p->ny * p->nz;
-  // Population offsets q*N + cell are 32-bit in the kernels.
+  // Population offsets (pop_ix, cells rounded up to blocks of 32) are 32-bit
+  // in the kernels.
   const long long qmax = p->dim == 2 ? 9 : 19;
-  if (N * qmax >= (1LL << 32)) return snprintf(msg, n, "Q * cells must be < 2^32 (%lld cells max)", ((1LL << 32) - 1) / qmax), PFLB_EINVAL;
+  if (((N + 31) / 32) * 32 * qmax >= (1LL << 32))
+    return snprintf(msg, n, "Q * cells must be < 2^32 (%lld cells max)", ((1LL << 32) - 1) / qmax / 32 * 32), PFLB_EINVAL;
   if (p->family < 0 || p->family > 3) return snprintf(msg, n, "unknown family %d", p->family), PFLB_EINVAL;
   if (p->storage < 0 || p->storage > 2) return snprintf(msg, n, "unknown storage %d", p->storage), PFLB_EINVAL;
   if (p->bc_y < 0 || p->bc_y > 2) return snprintf(msg, n, "bc_y must be 0, 1 or 2"), PFLB_EINVAL;
@@ -299,9 +301,13 @@ int pflb_create(const pflb_params* params, void* cuda_stream, pflb_handle** out)
     }
     return PFLB_OK;
   };
-  if ((rc = alloc(&h->g[0], (size_t)h->QG * h->N * h->elem))) return rc;
-  if ((rc = alloc(&h->g[1], (size_t)h->QG * h->N * h->elem))) return rc;
-  if ((rc = alloc(&h->f, (size_t)h->QF * h->N * h->elem))) return rc;
+  // Populations in blocks of kPopBlock cells (pop_ix), plus 16 bytes of
+  // padding: the step kernel fetches 16-bit populations as the aligned
+  // 32-bit words that contain them.
+  const size_t npad = (size_t)((h->N + kPopBlock - 1) / kPopBlock) * kPopBlock;
+  if ((rc = alloc(&h->g[0], (size_t)h->QG * npad * h->elem + 16))) return rc;
+  if ((rc = alloc(&h->g[1], (size_t)h->QG * npad * h->elem + 16))) return rc;
+  if ((rc = alloc(&h->f, (size_t)h->QF * npad * h->elem + 16))) return rc;
   if (h->family == 3 && (rc = alloc((void**)&h->phiu, (size_t)h->dim * h->N * sizeof(float)))) return rc;
   if ((rc = alloc((void**)&h->obs, (size_t)(h->obs_cap + 1) * sizeof(DevObs)))) return rc;
   if ((rc = alloc((void**)&h->gamma_acc, 6 * sizeof(double)))) return rc;

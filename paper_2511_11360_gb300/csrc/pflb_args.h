@@ -8,17 +8,14 @@ namespace pflb {
 
 // Tile of the single-domain step kernel: cells per block along the two fast
 // axes (ta x tb) and the resident blocks per SM its register budget is sized
-// for. FP32 storage stages the next plane's populations in shared memory and
-// needs up to 168 registers a thread (12 warps per SM); the 16-bit storage
-// reads them directly and runs 16 warps per SM at 128 registers.
+// for. Staging the next plane's populations in shared memory needs up to
+// 168 registers a thread in 3D (12 warps per SM). The storage type does not
+// change the shape (16-bit populations are staged as 32-bit words).
 struct TileShape {
   int ta, tb, minb;
 };
 __host__ __device__ constexpr TileShape tile_shape(int family, int dim, int storage) {
-  return dim == 2 ? TileShape{128, 1, 4}
-       : storage != 0 ? TileShape{32, 8, 2}
-       : family == 3 ? TileShape{32, 6, 2}
-       : TileShape{32, 4, 3};
+  return (void)storage, dim == 2 ? TileShape{128, 1, 4} : family == 3 ? TileShape{32, 6, 2} : TileShape{32, 4, 3};
 }
 
 struct StepArgs {

@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(256) gamma_kernel(const GammaArgs a) {
     float gv[QG];
 #pragma unroll
     for (int q = 0; q < QG; ++q)
-      gv[q] = (DIM == 3 && q == 0) ? 0.0f : pop_load<T, LG>(g + (long long)q * a.N + idx, q, P.gref);
+      gv[q] = (DIM == 3 && q == 0) ? 0.0f : pop_load<T, LG>(g + pop_ix<LG>(q, (unsigned)idx), q, P.gref);
     const float ps = phi_star<LG, DIM == 3>(gv);
     comp_add(h1, l1, P.four_beta_over_kappa * (ps - P.phiH) * (ps - P.phiL) * (ps - P.phi0));
     comp_add(h2, l2, (P.phiH - ps) * (ps - P.phiL));
@@ -102,7 +102,7 @@ __global__ void canon_kernel(const CanonArgs a) {
 #pragma unroll
     for (int q = 0; q < QG; ++q) {
       float* sp = a.state + (long long)q * N + idx;
-      T* gp = g + (long long)q * N + idx;
+      T* gp = g + pop_ix<LG>(q, (unsigned)idx);
       const bool skip = (DIM == 3 && !a.ch && q == 0);
       if (a.to_canon) *sp = skip ? 0.0f : pop_loadc<T, LG>(gp, q, P.gref);
       else if (!skip) pop_store<T, LG>(gp, q, *sp, P.gref);
@@ -130,7 +130,7 @@ __global__ void canon_kernel(const CanonArgs a) {
         }
       }
       float* sp = a.state + (long long)(QG + q) * N + idx;
-      T* fp = f + (long long)slot * N + src;
+      T* fp = f + pop_ix<LF>(slot, (unsigned)src);
       if (a.to_canon) *sp = pop_loadc<T, LF>(fp, q, 0.0f);
       else pop_store<T, LF>(fp, q, *sp, 0.0f);
     }

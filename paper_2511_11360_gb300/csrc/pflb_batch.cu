@@ -342,7 +342,9 @@ template <typename F>
 void for_each_piece(pflb_batch* b, F fn) {
   size_t off = 0;
   for (pflb_handle* h : b->dom) {
-    const size_t ng = (size_t)h->QG * h->N * h->elem, nf = (size_t)h->QF * h->N * h->elem;
+    // Population arrays hold Q x (N rounded up to the layout block).
+    const size_t npad = (size_t)((h->N + kPopBlock - 1) / kPopBlock) * kPopBlock;
+    const size_t ng = (size_t)h->QG * npad * h->elem, nf = (size_t)h->QF * npad * h->elem;
     fn(h, 0, off, ng);
     off += ng;
     fn(h, 1, off, nf);

@@ -52,18 +52,33 @@ __global__ void __launch_bounds__(TA, BatchGeom<TA>::MINB) batch_step_kernel(con
     __syncthreads();
     ObsPartial obs;
     obs_init(obs);
-    switch (e.fam) {
-      case FAM_FAKHARI:
-        step_tile<FAM_FAKHARI, 2, float, TA, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
+    // Widths that are a multiple of the population block take the
+    // constant-offset addressing (the sweep's widths all are).
+    const bool row = s_args.p.nx % (int)kPopBlock == 0;
+    switch (e.fam * 2 + (row ? 1 : 0)) {
+      case 2 * FAM_FAKHARI + 1:
+        step_tile<FAM_FAKHARI, 2, float, TA, 1, -1, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
         break;
-      case FAM_CHAI:
-        step_tile<FAM_CHAI, 2, float, TA, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
+      case 2 * FAM_FAKHARI:
+        step_tile<FAM_FAKHARI, 2, float, TA, 1, -1, 0>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
         break;
-      case FAM_HU:
-        step_tile<FAM_HU, 2, float, TA, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
+      case 2 * FAM_CHAI + 1:
+        step_tile<FAM_CHAI, 2, float, TA, 1, -1, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
+        break;
+      case 2 * FAM_CHAI:
+        step_tile<FAM_CHAI, 2, float, TA, 1, -1, 0>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
+        break;
+      case 2 * FAM_HU + 1:
+        step_tile<FAM_HU, 2, float, TA, 1, -1, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
+        break;
+      case 2 * FAM_HU:
+        step_tile<FAM_HU, 2, float, TA, 1, -1, 0>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
+        break;
+      case 2 * FAM_LIANG + 1:
+        step_tile<FAM_LIANG, 2, float, TA, 1, -1, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
         break;
       default:
-        step_tile<FAM_LIANG, 2, float, TA, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
+        step_tile<FAM_LIANG, 2, float, TA, 1, -1, 0>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
         break;
     }
     obs_block_commit(obs, s_args.obs_slot, s_red);
@@ -90,13 +105,12 @@ __global__ void __launch_bounds__(256) batch_gamma_kernel(const BatchGammaArgs g
     const BatchGammaEntry e = ga.ent[k];
     const StepArgs& A = ga.args[e.inst];
     const float* g = static_cast<const float*>(A.g_src);
-    const unsigned N = (unsigned)A.N;
     const float fbk = A.p.four_beta_over_kappa, pH = A.p.phiH, pL = A.p.phiL, p0 = A.p.phi0;
     float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
     for (int idx = e.begin + tid; idx < e.end; idx += 256) {
       float gv[9];
 #pragma unroll
-      for (int q = 0; q < 9; ++q) gv[q] = g[q * N + (unsigned)idx];
+      for (int q = 0; q < 9; ++q) gv[q] = g[pop_ix<LG>(q, (unsigned)idx)];
       const float ps = phi_star<LG, false>(gv);
       comp_add(h1, l1, fbk * (ps - pH) * (ps - pL) * (ps - p0));
       comp_add(h2, l2, (pH - ps) * (ps - pL));

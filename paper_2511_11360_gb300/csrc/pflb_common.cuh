@@ -101,6 +101,18 @@ __device__ __forceinline__ float wmul(int a, float x) {
   return fmaf(L::w(a), x, L::wlo(a) * x);
 }
 
+// Population layout in device memory (AoSoA): the linear cell index is cut
+// into blocks of 32 consecutive cells, and each block holds its Q velocity
+// planes one after another, so population q of cell i sits at element
+// ((i / 32) Q + q) 32 + i % 32. A warp over 32 aligned cells of a row then
+// reads or writes one contiguous 32 Q-element span instead of Q scattered
+// rows. Arrays hold Q x (N rounded up to 32) elements.
+constexpr unsigned kPopBlock = 32u;
+template <typename L>
+__host__ __device__ __forceinline__ unsigned pop_ix(int q, unsigned cell) {
+  return ((cell >> 5) * (unsigned)L::Q + (unsigned)q) * kPopBlock + (cell & (kPopBlock - 1u));
+}
+
 // Lattice triple per dimension: phase field g, hydrodynamics f, stencil.
 template <int DIM> struct Lattices;
 template <> struct Lattices<2> { using G = D2Q9; using F = D2Q9; using S = D2Q9; };
@@ -190,6 +202,7 @@ template <> struct Codec<__half> {
   __device__ __forceinline__ static __half ld(const __half* p) { return __ldg(p); }
   __device__ __forceinline__ static __half ldc(const __half* p) { return *p; }
   __device__ __forceinline__ static float dec(__half x, float s, float off) { return fmaf(__half2float(x), s, off); }
+  __device__ __forceinline__ static __half from_bits(unsigned short b) { return __ushort_as_half(b); }
   __device__ __forceinline__ static void st(__half* p, float v, float inv_s, float off) {
     *p = __float2half_rn((v - off) * inv_s);
   }
@@ -200,6 +213,7 @@ template <> struct Codec<__nv_bfloat16> {
   __device__ __forceinline__ static float dec(__nv_bfloat16 x, float s, float off) {
     return fmaf(__bfloat162float(x), s, off);
   }
+  __device__ __forceinline__ static __nv_bfloat16 from_bits(unsigned short b) { return __ushort_as_bfloat16(b); }
   __device__ __forceinline__ static void st(__nv_bfloat16* p, float v, float inv_s, float off) {
     *p = __float2bfloat16_rn((v - off) * inv_s);
   }
@@ -225,6 +239,14 @@ __device__ __forceinline__ float pop_load(const T* p, int q, float c) {  // read
 template <typename T, typename L>
 __device__ __forceinline__ float pop_loadc(const T* p, int q, float c) { // data written in this kernel
   return Codec<T>::dec(Codec<T>::ldc(p), pow2_scale<L>(q), wprime<L>(q) * c);
+}
+// A 16-bit population staged as the aligned 32-bit word that holds it:
+// hi selects the upper half.
+template <typename T, typename L>
+__device__ __forceinline__ float pop_from_word(float word, unsigned hi, int q, float c) {
+  const unsigned w = __float_as_uint(word);
+  const unsigned short b = (unsigned short)(hi ? (w >> 16) : (w & 0xffffu));
+  return Codec<T>::dec(Codec<T>::from_bits(b), pow2_scale<L>(q), wprime<L>(q) * c);
 }
 template <typename T, typename L>
 __device__ __forceinline__ void pop_store(T* p, int q, float v, float c) {

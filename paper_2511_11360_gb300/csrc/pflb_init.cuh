@@ -60,7 +60,7 @@ __global__ void init_kernel(const InitArgs args) {
       if constexpr (FAM == FAM_FAKHARI) geq = w * phi * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * usq);
       else if constexpr (FAM == FAM_LIANG) geq = (q == 0) ? phi + (w - 1.0f) * P.eta * mu : w * (P.eta * mu + 3.0f * phi * eu);
       else geq = w * phi * (1.0f + 3.0f * eu);
-      pop_store<T, LG>(g + (long long)q * N + idx, q, geq, P.gref);
+      pop_store<T, LG>(g + pop_ix<LG>(q, (unsigned)idx), q, geq, P.gref);
     }
 #pragma unroll
     for (int q = 0; q < QF; ++q) {
@@ -73,7 +73,7 @@ __global__ void init_kernel(const InitArgs args) {
         feq = (q == 0) ? rho * w * (-1.5f * usq) : rho * w * (3.0f * eu + 4.5f * eu * eu - 1.5f * usq);
       else
         feq = w * (3.0f * eu + 4.5f * eu * eu - 1.5f * usq);
-      pop_store<T, LF>(f + (long long)q * N + idx, q, feq, 0.0f);
+      pop_store<T, LF>(f + pop_ix<LF>(q, (unsigned)idx), q, feq, 0.0f);
     }
     if constexpr (FAM == FAM_LIANG) {
 #pragma unroll

@@ -333,12 +333,14 @@ struct TileSmem {
   static constexpr int NSLOT = CH ? 8 : 4;
   static constexpr int PHI = NSLOT * PLANE;
   static constexpr int MU = CH ? 4 * (TA + 2) * (TB + 2 * ((DIM == 3) ? 1 : 0)) : 1;
-  // FP32 storage stages the next plane's populations asynchronously: two
-  // stages of f (Q_f per cell) and g (Q_g per cell of the tile and halo).
-  static constexpr bool STAGED = std::is_same<T, float>::value;
+  // The populations of the next planes are staged asynchronously: NST stages
+  // of f (Q_f words per cell) and g (Q_g words per cell of the tile and
+  // halo); a 16-bit population is staged as the aligned 32-bit word holding it.
+  static constexpr bool STAGED = true;
   static constexpr int FST = Lattices<DIM>::F::Q * NT;
   static constexpr int GST = Lattices<DIM>::G::Q * PLANE;
-  static constexpr int STAGE = STAGED ? 2 * (FST + GST) : 0;
+  static constexpr int NST = 3;   // stages: plane c is consumed while c+1, c+2 are in flight
+  static constexpr int STAGE = STAGED ? NST * (FST + GST) : 0;
   static constexpr size_t BYTES = (size_t)(STAGE + PHI + MU) * sizeof(float);
 };
 
@@ -348,7 +350,7 @@ struct TileSmem {
 // kernel (one tile per block) and by the persistent batch kernel (tiles of
 // many domains claimed in turn). Accumulates the observables into obs.
 // ---------------------------------------------------------------------------
-template <int FAM, int DIM, typename T, int TA, int TB, int PAR = -1>
+template <int FAM, int DIM, typename T, int TA, int TB, int PAR = -1, int ROW = -1>
 __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, int c0, int chunk,
                                           float* __restrict__ s_phi, float* __restrict__ s_mu,
                                           float* __restrict__ s_stage, ObsPartial& obs) {
@@ -371,6 +373,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
   constexpr int KM = (MHALO + NT - 1) / NT;
   constexpr bool STAGED = TileSmem<FAM, DIM, T, TA, TB>::STAGED;
   constexpr int FST = TileSmem<FAM, DIM, T, TA, TB>::FST, GST = TileSmem<FAM, DIM, T, TA, TB>::GST;
+  constexpr int NST = TileSmem<FAM, DIM, T, TA, TB>::NST;
   constexpr bool SKIP0 = (DIM == 3 && !CH);   // D3Q7 rest slot of the AC families: w_0 = 0, g_0 = 0
   (void)RB;
 
@@ -442,7 +445,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
 #pragma unroll
     for (int q = 0; q < QG; ++q) {
       if (DIM == 3 && !CH && q == 0) { gv[q] = 0.0f; continue; }  // D3Q7 rest slot: w_0 = 0, g_0 = 0
-      gv[q] = pop_load<T, LG>(gsrc + (q * N + idx), q, P.gref);
+      gv[q] = pop_load<T, LG>(gsrc + pop_ix<LG>(q, idx), q, P.gref);
     }
     return phi_star<LG, (DIM == 3 && !CH)>(gv);
   };
@@ -516,58 +519,133 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
   auto A_of = [&](int d) { return d < 0 ? am : (d > 0 ? ap : aw); };
   auto RB_of = [&](int d) { return d < 0 ? rbm : (d > 0 ? rbp : rbw); };
 
+  // Element offsets in the block layout (pop_ix). When nx is a multiple of
+  // the block width, shifting a cell by whole rows or planes moves each of
+  // its populations by a multiple of the block stride, so the offset of
+  // population q of the neighbour (x + da, y + db) on plane cs is
+  //   E0 + D_x(da) + D_y(db) + cs * Q * nx * ny + 32 q
+  // with per-thread constants E0, D_x, D_y (periodic wrap included) and the
+  // velocity's part an immediate. Otherwise the cell index is formed and
+  // mapped (pop_ix) per access.
+  // ROW: 1 = nx is a multiple of the block width, 0 = it is not, -1 = test here.
+  const bool rowal = ROW >= 0 ? ROW == 1 : (NA % (int)kPopBlock) == 0;
+  const unsigned cell0 = (unsigned)(aw + rbw);
+  const unsigned fE0 = pop_ix<LF>(0, cell0), gE0 = pop_ix<LG>(0, cell0);
+  const unsigned fdxm = pop_ix<LF>(0, (unsigned)(am + rbw)) - fE0, fdxp = pop_ix<LF>(0, (unsigned)(ap + rbw)) - fE0;
+  const unsigned fdym = pop_ix<LF>(0, (unsigned)(aw + rbm)) - fE0, fdyp = pop_ix<LF>(0, (unsigned)(aw + rbp)) - fE0;
+  const unsigned gdxm = pop_ix<LG>(0, (unsigned)(am + rbw)) - gE0, gdxp = pop_ix<LG>(0, (unsigned)(ap + rbw)) - gE0;
+  const unsigned gdym = pop_ix<LG>(0, (unsigned)(aw + rbm)) - gE0, gdyp = pop_ix<LG>(0, (unsigned)(aw + rbp)) - gE0;
+  const unsigned fplane = (unsigned)NAB * (unsigned)QF, gplane = (unsigned)NAB * (unsigned)QG;
+  // Population q of the cell (x + da, y + db) on plane cs (cs already wrapped).
+  auto f_at = [&](int q, int da, int db, int cs) -> unsigned {
+    if (rowal)
+      return fE0 + (da < 0 ? fdxm : (da > 0 ? fdxp : 0u)) + (db < 0 ? fdym : (db > 0 ? fdyp : 0u)) +
+             (unsigned)cs * fplane + (unsigned)q * kPopBlock;
+    return pop_ix<LF>(q, (unsigned)(A_of(da) + RB_of(db) + cs * NAB));
+  };
+  auto g_at = [&](int q, int da, int db, int cs) -> unsigned {
+    if (rowal)
+      return gE0 + (da < 0 ? gdxm : (da > 0 ? gdxp : 0u)) + (db < 0 ? gdym : (db > 0 ? gdyp : 0u)) +
+             (unsigned)cs * gplane + (unsigned)q * kPopBlock;
+    return pop_ix<LG>(q, (unsigned)(A_of(da) + RB_of(db) + cs * NAB));
+  };
+  // Plane reached from c by dc (periodic, or c itself at a wall).
+  auto plane_of = [&](int c, int dc) -> int {
+    return dc < 0 ? (c == 0 ? NC - 1 : c - 1) : (dc > 0 ? (c == NC - 1 ? 0 : c + 1) : c);
+  };
+
   // Element offset of the f population q the own cell reads at plane c (AA
   // pattern): even steps its own slot q; odd steps slot opp(q) of x - e_q,
   // or its own slot q where x - e_q lies beyond a wall.
   auto f_read_ofs = [&](int c, int q) -> unsigned {
     const int da = da_of<DIM, LF>(q), db = db_of<DIM, LF>(q), dc = dc_of<DIM, LF>(q);
     const bool cross = walls && ((dc > 0 && c == 0) || (dc < 0 && c == NC - 1));
-    if (parity == 0 || cross) return q * N + (unsigned)(aw + rbw + c * NAB);
-    const int cs = dc > 0 ? (c == 0 ? NC - 1 : c - 1) : (dc < 0 ? (c == NC - 1 ? 0 : c + 1) : c);
-    return LF::opp(q) * N + (unsigned)(A_of(-da) + RB_of(-db) + cs * NAB);
+    if (parity == 0 || cross) return f_at(q, 0, 0, c);
+    return f_at(LF::opp(q), -da, -db, plane_of(c, -dc));
+  };
+  // Own and halo g of plane cg: the halo cells' offsets relative to their
+  // plane are per-thread constants in the row-aligned case.
+  unsigned gHalo0[KH];
+#pragma unroll
+  for (int k = 0; k < KH; ++k) gHalo0[k] = pop_ix<LG>(0, (unsigned)halo_ab[k]);
+  const unsigned gOwn0 = pop_ix<LG>(0, (unsigned)own_ab);
+  auto g_src_ofs = [&](int q, int k, int cm) -> unsigned {   // k < 0: own cell; cm: mapped plane
+    if (rowal) return (k < 0 ? gOwn0 : gHalo0[k]) + (unsigned)cm * gplane + (unsigned)q * kPopBlock;
+    return pop_ix<LG>(q, (unsigned)((k < 0 ? own_ab : halo_ab[k]) + NAB * cm));
   };
 
-  // FP32 storage: the incoming g of plane cg (own cell and this thread's
-  // halo cells) and the own cell's f of plane cf are copied asynchronously
-  // into this thread's slots of stage s a plane before they are used. Each
-  // thread reads back only its own slots, so completing its own copies
-  // (cp.async.wait_group) is all the synchronisation needed.
+  // The incoming g of plane cg (own cell and this thread's halo cells) and
+  // the own cell's f of plane cf are copied asynchronously into this
+  // thread's slots of stage s a plane before they are used. Each thread
+  // reads back only its own slots, so completing its own copies
+  // (cp.async.wait_group) is all the synchronisation needed. cp.async moves
+  // at least 4 aligned bytes: a 16-bit population is fetched as the aligned
+  // word that contains it (its neighbour's half is ignored; the arrays are
+  // allocated with padding so the last word is in bounds), and a bit of
+  // gm/fm records which half is ours.
+  constexpr bool WIDE = sizeof(T) == 4;
+  static_assert((1 + KH) * QG <= 32, "half-select bits of the staged g");
   auto stage_f = [&](int s) { return s_stage + s * (FST + GST); };
   auto stage_g = [&](int s) { return s_stage + s * (FST + GST) + FST; };
-  auto issue = [&](int cg, int cf, int s) {
-    const float* gs32 = reinterpret_cast<const float*>(gsrc);
-    const float* fb32 = reinterpret_cast<const float*>(fb);
+  auto word_of = [&](const T* base, unsigned e, unsigned& bits, int bit) -> const float* {
+    if constexpr (WIDE) {
+      (void)bits;
+      (void)bit;
+      return reinterpret_cast<const float*>(base + e);
+    } else {
+      bits |= (e & 1u) << bit;
+      return reinterpret_cast<const float*>(base + (e & ~1u));
+    }
+  };
+  auto issue = [&](int cg, int cf, int s, unsigned& gm, unsigned& fm) {
     float* gs = stage_g(s);
-    const unsigned pofs = (unsigned)(NAB * map_c(cg));
+    gm = 0u;
+    fm = 0u;
+    const int cm = map_c(cg);
 #pragma unroll
-    for (int q = SKIP0 ? 1 : 0; q < QG; ++q) cp_async4(gs + q * PLANE + tid, gs32 + (q * N + own_ab + pofs));
+    for (int q = SKIP0 ? 1 : 0; q < QG; ++q)
+      cp_async4(gs + q * PLANE + tid, word_of(gsrc, g_src_ofs(q, -1, cm), gm, q));
 #pragma unroll
     for (int k = 0; k < KH; ++k) {
       if (halo_pos[k] >= 0) {
 #pragma unroll
         for (int q = SKIP0 ? 1 : 0; q < QG; ++q)
-          cp_async4(gs + q * PLANE + NT + tid + k * NT, gs32 + (q * N + halo_ab[k] + pofs));
+          cp_async4(gs + q * PLANE + NT + tid + k * NT, word_of(gsrc, g_src_ofs(q, k, cm), gm, (1 + k) * QG + q));
       }
     }
     if (active) {
       float* fs = stage_f(s);
 #pragma unroll
-      for (int q = 0; q < QF; ++q) cp_async4(fs + q * NT + tid, fb32 + f_read_ofs(cf, q));
+      for (int q = 0; q < QF; ++q) cp_async4(fs + q * NT + tid, word_of(fb, f_read_ofs(cf, q), fm, q));
+    }
+  };
+  // Decode one staged population.
+  auto staged = [&](float word, unsigned bits, int bit, int q, bool is_g) -> float {
+    if constexpr (WIDE) {
+      (void)bits;
+      (void)bit;
+      (void)q;
+      (void)is_g;
+      return word;
+    } else {
+      const unsigned hi = (bits >> bit) & 1u;
+      return is_g ? pop_from_word<T, LG>(word, hi, q, P.gref) : pop_from_word<T, LF>(word, hi, q, 0.0f);
     }
   };
   // phi of logical plane c from stage s into the ring; keeps the own cell's g.
-  auto produce_staged = [&](int c, int s, float (&gown)[QG]) {
+  auto produce_staged = [&](int c, int s, unsigned gm, float (&gown)[QG]) {
     const float* gs = stage_g(s);
     float* slot = ring(c);
 #pragma unroll
-    for (int q = 0; q < QG; ++q) gown[q] = (SKIP0 && q == 0) ? 0.0f : gs[q * PLANE + tid];
+    for (int q = 0; q < QG; ++q) gown[q] = (SKIP0 && q == 0) ? 0.0f : staged(gs[q * PLANE + tid], gm, q, q, true);
     slot[own_slot] = finish_phi<FAM>(P, phi_star<LG, SKIP0>(gown), gamma);
 #pragma unroll
     for (int k = 0; k < KH; ++k) {
       if (halo_pos[k] >= 0) {
         float tmp[QG];
 #pragma unroll
-        for (int q = 0; q < QG; ++q) tmp[q] = (SKIP0 && q == 0) ? 0.0f : gs[q * PLANE + NT + tid + k * NT];
+        for (int q = 0; q < QG; ++q)
+          tmp[q] = (SKIP0 && q == 0) ? 0.0f : staged(gs[q * PLANE + NT + tid + k * NT], gm, (1 + k) * QG + q, q, true);
         slot[halo_pos[k]] = finish_phi<FAM>(P, phi_star<LG, SKIP0>(tmp), gamma);
       }
     }
@@ -582,11 +660,17 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
     produce(c0, g0);
     if constexpr (CH) produce(c0 + 1, g1);
   }
+  // Half-select bits of the staged planes c, c+1, ..., c+NST-1 (index 0 is
+  // the plane being collided; rotated every plane, compile-time indices).
+  unsigned gmq[NST], fmq[NST];
+  int st = 0;   // stage holding plane c
   if constexpr (STAGED) {
-    issue(c0 + H, c0, 0);
-    cp_async_commit();
-    if (c0 + 1 < c1) issue(c0 + 1 + H, c0 + 1, 1);
-    cp_async_commit();
+#pragma unroll
+    for (int k = 0; k < NST; ++k) {
+      gmq[k] = fmq[k] = 0u;
+      if (c0 + k < c1) issue(c0 + k + H, c0 + k, k, gmq[k], fmq[k]);
+      cp_async_commit();
+    }
   }
   if constexpr (CH) {
     __syncthreads();
@@ -595,16 +679,16 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
   }
 
   for (int c = c0; c < c1; ++c) {
-    const int st = (c - c0) & 1;
-    if constexpr (STAGED) cp_async_wait<1>();   // stage st (plane c) has landed; c + 1 may be in flight
+    const unsigned gms = gmq[0], fms = fmq[0];
+    if constexpr (STAGED) cp_async_wait<NST - 1>();   // plane c has landed; the later ones may be in flight
     if constexpr (CH) {
-      if constexpr (STAGED) produce_staged(c + 2, st, g2);
+      if constexpr (STAGED) produce_staged(c + 2, st, gms, g2);
       else produce(c + 2, g2);
       __syncthreads();
       make_mu(c + 1);
       __syncthreads();
     } else {
-      if constexpr (STAGED) produce_staged(c + 1, st, g1);
+      if constexpr (STAGED) produce_staged(c + 1, st, gms, g1);
       else produce(c + 1, g1);
       __syncthreads();
     }
@@ -644,22 +728,16 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
         lmu = Sym<LS>::lap(nb, mu_c);
       }
 
-      const int cm = (c == 0) ? NC - 1 : c - 1, cp = (c == NC - 1) ? 0 : c + 1;
       const bool lo_wall = walls && c == 0, hi_wall = walls && c == NC - 1;
-      const int pcm = cm * NAB, pc0 = c * NAB, pcp = cp * NAB;
-      auto PC_of = [&](int d) { return d < 0 ? pcm : (d > 0 ? pcp : pc0); };
       auto crosses = [&](int dcv) { return (dcv < 0 && lo_wall) || (dcv > 0 && hi_wall); };
-      const unsigned idx = (unsigned)(aw + rbw + pc0);
-      auto nidx = [&](int da, int db, int dc) -> unsigned {
-        return (unsigned)(A_of(da) + RB_of(db) + PC_of(dc));
-      };
+      const unsigned idx = (unsigned)(aw + rbw + c * NAB);
 
       // Pre-collision f (AA pattern).
       float f[QF];
       if constexpr (STAGED) {
         const float* fs = stage_f(st);
 #pragma unroll
-        for (int q = 0; q < QF; ++q) f[q] = fs[q * NT + tid];
+        for (int q = 0; q < QF; ++q) f[q] = staged(fs[q * NT + tid], fms, q, q, false);
       } else {
 #pragma unroll
         for (int q = 0; q < QF; ++q) f[q] = pop_loadc<T, LF>(fb + f_read_ofs(c, q), q, 0.0f);
@@ -693,7 +771,8 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
         obs.count += (pc > P.phi0) ? 1u : 0u;
         obs.mx = fmaxf(obs.mx, pc);
         obs.mn = fminf(obs.mn, pc);
-        if (!(isfinite(pc) && isfinite(usq) && rho > 0.0f)) obs.bad = 1u;
+        // Instability (rho <= 0, non-finite phi or u) is judged once per thread
+        // after the march: a non-finite value propagates into the sums.
       }
 
       if (args.macro) {
@@ -713,13 +792,13 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
           if (DIM == 3 && !CH && q == 0) continue;
           const int da = da_of<DIM, LG>(q), db = db_of<DIM, LG>(q), dc = dc_of<DIM, LG>(q);
           if (P.freeze) {
-            pop_store<T, LG>(gdst + (q * N + idx), q, g0[q], P.gref);
+            pop_store<T, LG>(gdst + g_at(q, 0, 0, c), q, g0[q], P.gref);
           } else if (crosses(dc)) {
             const float uw = dc < 0 ? uw_lo : uw_hi;
             const float v = gnew[q] - 6.0f * LG::w(q) * pc * (float)LG::ex(q) * uw;
-            pop_store<T, LG>(gdst + (LG::opp(q) * N + idx), q, v, P.gref);
+            pop_store<T, LG>(gdst + g_at(LG::opp(q), 0, 0, c), q, v, P.gref);
           } else {
-            pop_store<T, LG>(gdst + (q * N + nidx(da, db, dc)), q, gnew[q], P.gref);
+            pop_store<T, LG>(gdst + g_at(q, da, db, plane_of(c, dc)), q, gnew[q], P.gref);
           }
         }
         // f: AA pattern.
@@ -734,19 +813,28 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
             v -= 6.0f * LF::w(q) * sc * (float)LF::ex(q) * uw;
           }
           if (parity == 0 || cr) {
-            pop_store<T, LF>(fb + (LF::opp(q) * N + idx), q, v, 0.0f);
+            pop_store<T, LF>(fb + f_at(LF::opp(q), 0, 0, c), q, v, 0.0f);
           } else {
-            pop_store<T, LF>(fb + (q * N + nidx(da, db, dc)), q, v, 0.0f);
+            pop_store<T, LF>(fb + f_at(q, da, db, plane_of(c, dc)), q, v, 0.0f);
           }
         }
       }
     }
 
-    // Refill the stage just consumed with plane c + 2 (issued here, where
-    // the fewest values are live).
+    // Refill the stage just consumed with plane c + NST (issued here, where
+    // the fewest values are live), and rotate the half-select bits.
     if constexpr (STAGED) {
-      if (c + 2 < c1) issue(c + 2 + H, c + 2, st);
+      unsigned gnext = 0u, fnext = 0u;
+      if (c + NST < c1) issue(c + NST + H, c + NST, st, gnext, fnext);
       cp_async_commit();
+#pragma unroll
+      for (int k = 0; k + 1 < NST; ++k) {
+        gmq[k] = gmq[k + 1];
+        fmq[k] = fmq[k + 1];
+      }
+      gmq[NST - 1] = gnext;
+      fmq[NST - 1] = fnext;
+      st = (st + 1 == NST) ? 0 : st + 1;
     }
 
     // Rotate the own-cell g pipeline.
@@ -761,12 +849,19 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
   // thread (inactive threads added nothing to vs).
   obs.cx += (float)aw * obs.vs;
   if constexpr (DIM == 3) obs.cy += (float)bw * obs.vs;
+  // A non-finite phi or u at any cell makes the phi or kinetic-energy sum
+  // non-finite; rho is linear in phi, so its minimum over the cells is
+  // attained at phi_min or phi_max (mn <= mx once a cell was visited).
+  if (obs.mn <= obs.mx) {
+    const float r1 = P.rhoL + P.drho_dphi * (obs.mn - P.phiL), r2 = P.rhoL + P.drho_dphi * (obs.mx - P.phiL);
+    if (!(isfinite(obs.s_hi) && isfinite(obs.ke) && r1 > 0.0f && r2 > 0.0f)) obs.bad = 1u;
+  }
 }
 
 // ---------------------------------------------------------------------------
 // The single-domain kernel: one tile per block.
 // ---------------------------------------------------------------------------
-template <int FAM, int DIM, typename T, int PAR>
+template <int FAM, int DIM, typename T, int PAR, int ROW>
 __global__ void __launch_bounds__(Geom<FAM, DIM, T>::TA * Geom<FAM, DIM, T>::TB, Geom<FAM, DIM, T>::MINB)
 step_kernel(const StepArgs args) {
   constexpr int TA = Geom<FAM, DIM, T>::TA, TB = Geom<FAM, DIM, T>::TB;
@@ -787,29 +882,35 @@ step_kernel(const StepArgs args) {
     obs_zero_slot(args.obs_zero);
   ObsPartial obs;
   obs_init(obs);
-  step_tile<FAM, DIM, T, TA, TB, PAR>(args, ti * TA, tj * TB, bid * args.chunk, args.chunk, s_phi, s_mu, s_stage,
-                                      obs);
+  step_tile<FAM, DIM, T, TA, TB, PAR, ROW>(args, ti * TA, tj * TB, bid * args.chunk, args.chunk, s_phi, s_mu,
+                                           s_stage, obs);
   obs_block_commit(obs, args.obs_slot, s_red);
 }
 
-template <int FAM, int DIM, typename T, int PAR>
+template <int FAM, int DIM, typename T, int PAR, int ROW>
 void launch_step_par(const StepArgs& args, cudaStream_t stream) {
   constexpr int TA = Geom<FAM, DIM, T>::TA, TB = Geom<FAM, DIM, T>::TB;
   constexpr size_t smem = TileSmem<FAM, DIM, T, TA, TB>::BYTES;
   static const cudaError_t attr = cudaFuncSetAttribute(
-      step_kernel<FAM, DIM, T, PAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      step_kernel<FAM, DIM, T, PAR, ROW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   (void)attr;
   const int NA = args.p.nx, NB = (DIM == 3) ? args.p.ny : 1, NC = (DIM == 3) ? args.p.nz : args.p.ny;
   const long long tiles = (long long)((NA + TA - 1) / TA) * ((NB + TB - 1) / TB);
   const long long chunks = (NC + args.chunk - 1) / args.chunk;
   dim3 block(TA, TB, 1);
-  step_kernel<FAM, DIM, T, PAR><<<(unsigned)(tiles * chunks), block, smem, stream>>>(args);
+  step_kernel<FAM, DIM, T, PAR, ROW><<<(unsigned)(tiles * chunks), block, smem, stream>>>(args);
 }
 
 template <int FAM, int DIM, typename T>
 void launch_step(const StepArgs& args, cudaStream_t stream) {
-  if (args.parity) launch_step_par<FAM, DIM, T, 1>(args, stream);
-  else launch_step_par<FAM, DIM, T, 0>(args, stream);
+  const bool row = args.p.nx % (int)kPopBlock == 0;
+  if (args.parity) {
+    if (row) launch_step_par<FAM, DIM, T, 1, 1>(args, stream);
+    else launch_step_par<FAM, DIM, T, 1, 0>(args, stream);
+  } else {
+    if (row) launch_step_par<FAM, DIM, T, 0, 1>(args, stream);
+    else launch_step_par<FAM, DIM, T, 0, 0>(args, stream);
+  }
 }
 
 }  // namespace pflb
