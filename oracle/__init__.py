@@ -9,7 +9,7 @@ The oracle restates, in plain numpy at float64, the equations of
 "Comparative study and critical assessment of phase-field lattice Boltzmann
 models for laminar and turbulent two-phase flow simulations" (arXiv
 2511.11360): Sec. II B (the shared BGK lattice Boltzmann equations), Sec. II C
-(Fakhari2017, Chai2018, Hu2019), Sec. II D (Liang2014), and the isotropic
+(Fakhari2017, Liang2018, Chai2018, Hu2019), Sec. II D (Liang2014), and the isotropic
 central stencils of Sec. III. Every function cites the passage it follows.
 Readings of passages the paper leaves silent or ambiguous are marked
 ``Reading R<n>``; the list is kept in the repository's design notes.

@@ -17,7 +17,8 @@ y = -1/2 and y = ny - 1/2 with halfway bounce-back (Reading R9).
 
 Families: FAKHARI2017 (conservative AC, Sec. II C 1), CHAI2018 (nonlocal AC,
 Sec. II C 3), HU2019 (hybrid AC, Sec. II C 4), LIANG2014 (Cahn-Hilliard,
-Sec. II D 1).
+Sec. II D 1), LIANG2018 (conservative AC with the conservative form of the
+Navier-Stokes equations, Sec. II C 2).
 
 Parity pins: tests/test_oracle_pins.py and tests/test_oracle_physics.py.
 """
@@ -27,21 +28,24 @@ import math
 import numpy as np
 
 __all__ = [
-    "FAKHARI2017", "CHAI2018", "HU2019", "LIANG2014", "FAMILY_NAMES",
+    "FAKHARI2017", "CHAI2018", "HU2019", "LIANG2014", "LIANG2018", "FAMILY_NAMES",
     "Lattice", "D2Q9", "D3Q19", "D3Q7", "lattices_for",
     "default_params", "derived", "State",
     "gradient", "laplacian", "lagrange_gamma", "nonlocal_R",
     "density", "kinematic_viscosity",
     "geq_fakhari", "geq_chai", "geq_liang2014",
     "feq_velocity", "feq_pressure",
-    "source_conservative", "force_fakhari", "force_guo", "force_liang2014",
+    "source_conservative", "force_fakhari", "force_guo", "force_liang2014", "force_liang2018",
     "macroscopic", "collide", "stream", "init_state", "step", "run",
     "observables", "step_at_cells", "pack_state", "unpack_state",
 ]
 
-FAKHARI2017, CHAI2018, HU2019, LIANG2014 = 0, 1, 2, 3
+FAKHARI2017, CHAI2018, HU2019, LIANG2014, LIANG2018 = 0, 1, 2, 3, 4
 FAMILY_NAMES = {FAKHARI2017: "fakhari2017", CHAI2018: "chai2018",
-                HU2019: "hu2019", LIANG2014: "liang2014"}
+                HU2019: "hu2019", LIANG2014: "liang2014", LIANG2018: "liang2018"}
+# Families that carry phi*u of the previous step for the backward-Euler
+# d_t(phi u) of Sec. III B.
+PHIU_FAMILIES = (LIANG2014, LIANG2018)
 
 CS2 = 1.0 / 3.0
 
@@ -266,7 +270,8 @@ def geq_fakhari(lat, phi, u):
 
 
 def geq_chai(lat, phi, u):
-    """g_eq = w phi (1 + e.u/c_s^2)      Eq. (Chai_geq); also Hu2019 (Sec. II C 4)."""
+    """g_eq = w phi (1 + e.u/c_s^2)      Eq. (Chai_geq); also Hu2019 (Sec. II C 4)
+    and Liang2018, whose Eq. (liang_geq) is the same first-order form."""
     eu = _edot(lat, u)
     w = lat.w.astype(phi.dtype).reshape((-1,) + (1,) * phi.ndim)
     return w * phi * (1.0 + eu / lat.cs2)
@@ -359,6 +364,18 @@ def force_liang2014(lat, u, grad_rho, Ftot):
     e_minus_u_dot_a = _edot(lat, vec_a) - np.sum(u * vec_a, axis=0)
     e_minus_u_dot_F = _edot(lat, Ftot) - np.sum(u * Ftot, axis=0)
     return (Gam * e_minus_u_dot_a + s * e_minus_u_dot_F) / cs2
+
+
+def force_liang2018(lat, u, grad_rho, F):
+    """Eq. (liang_F_final), as printed:
+    F_b = w [ u.grad(rho) + e.F/c_s^2 + u grad(rho) : (e e - c_s^2 I)/c_s^2 ],
+    with u grad(rho) : (e e - c_s^2 I) = (e.u)(e.grad rho) - c_s^2 u.grad(rho)
+    and F = F_s + F_b."""
+    cs2 = lat.cs2
+    w = lat.w.astype(u.dtype).reshape((-1,) + (1,) * (u.ndim - 1))
+    ugr = np.sum(u * grad_rho, axis=0)
+    dyad = _edot(lat, u) * _edot(lat, grad_rho) - cs2 * ugr
+    return w * (ugr + _edot(lat, F) / cs2 + dyad / cs2)
 
 
 # --------------------------------------------------------------------------
@@ -462,6 +479,19 @@ def macroscopic(P, st, gamma=None):
         m.update(lap_mu=lap_mu, Fa=Fa, p=p, u=u, F=F, Fs=Fs, Fb=Fb + FL)
         return m
 
+    if fam == LIANG2018:
+        # Eq. (liang_velocity_update), rho u = sum e f + F dt/2 with
+        # F = F_s + F_b; the linear forcing A rho u is solved for exactly.
+        u = (mom + 0.5 * (Fs + Fb)) / (rho * (1.0 - 0.5 * A))
+        FL = A * rho * u
+        F = Fs + Fb + FL
+        # Pressure, Eq. (liang_p_update).
+        w0 = float(lf.w[0])
+        p = lf.cs2 / (1.0 - w0) * (f[1:].sum(axis=0) + 0.5 * np.sum(u * grad_rho, axis=0)
+                                   + rho * w0 * (-_udotu(u) / (2 * lf.cs2)))
+        m.update(p=p, u=u, F=F, Fs=Fs, Fb=Fb + FL)
+        return m
+
     # Fakhari2017 / Chai2018 / Hu2019 hydrodynamics (Sec. II C 1, II C 3).
     # Pressure p = rho c_s^2 sum f, Eq. (fakhari_p_update); Reading R4 uses the
     # same thermodynamic pressure for Chai2018/Hu2019.
@@ -512,6 +542,12 @@ def collide(P, st, m):
         w = lg.w.astype(phi.dtype).reshape((-1,) + (1,) * phi.ndim)
         lam = m["lam"]
         G = lam * source_conservative(P, lg, phi, m["grad_phi"]) + (1.0 - lam) * w * m["R"]  # Eq. (Hu_G)
+    elif fam == LIANG2018:
+        geq = geq_chai(lg, phi, u)                            # Eq. (liang_geq)
+        phiu_new = phi * u
+        dtphiu = phiu_new - st.phiu_prev                      # backward Euler, Sec. III B
+        w = lg.w.astype(phi.dtype).reshape((-1,) + (1,) * phi.ndim)
+        G = w * _edot(lg, dtphiu) / lg.cs2 + source_conservative(P, lg, phi, m["grad_phi"])  # Eq. (liang_G_final)
     elif fam == LIANG2014:
         geq = geq_liang2014(lg, phi, u, m["mu"], P["eta_ch"])
         phiu_new = phi * u
@@ -528,6 +564,9 @@ def collide(P, st, m):
     if fam == LIANG2014:
         feq = feq_pressure(lf, m["p"], rho, u)
         Fb = force_liang2014(lf, u, m["grad_rho"], m["F"])
+    elif fam == LIANG2018:
+        feq = feq_pressure(lf, m["p"], rho, u)                 # Eq. (liang_feq)
+        Fb = force_liang2018(lf, u, m["grad_rho"], m["F"])
     else:
         feq = feq_velocity(lf, m["p"] / (rho * lf.cs2), u)
         if fam == FAKHARI2017:
@@ -592,13 +631,16 @@ def init_state(P, phi0, u0, dtype=np.float64):
         g = geq_fakhari(lg, phi0, u0)
     elif fam in (CHAI2018, HU2019):
         g = geq_chai(lg, phi0, u0)
+    elif fam == LIANG2018:
+        g = geq_chai(lg, phi0, u0)
+        phiu = phi0 * u0
     else:
         c = derived(P)
         mu = 4.0 * c["beta"] * (phi0 - P["phi_H"]) * (phi0 - P["phi_L"]) * (phi0 - c["phi0"]) \
             - c["kappa"] * laplacian(phi0, ls, _walls(P))
         g = geq_liang2014(lg, phi0, u0, mu, P["eta_ch"])
         phiu = phi0 * u0
-    if fam == LIANG2014:
+    if fam in (LIANG2014, LIANG2018):
         f = feq_pressure(lf, np.zeros_like(rho), rho, u0)
     else:
         f = feq_velocity(lf, np.zeros_like(rho), u0)
@@ -614,7 +656,7 @@ def step(P, st, gamma=None):
         g_new = st.g.copy()               # Sec. III D: phase-field evolution disabled
     else:
         g_new = stream(P, lg, gs, m["phi"])
-    f_scale = m["rho"] if P["family"] == LIANG2014 else np.ones_like(m["rho"])
+    f_scale = m["rho"] if P["family"] in (LIANG2014, LIANG2018) else np.ones_like(m["rho"])
     f_new = stream(P, lf, fs, f_scale)
     return State(g_new, f_new, phiu_new, st.t + 1)
 
@@ -700,10 +742,10 @@ def step_at_cells(P, st, cells, gamma=None):
 # Flat state vector (the canonical population blob of the C ABI)
 # --------------------------------------------------------------------------
 def pack_state(P, st):
-    """Concatenate g (Qg x N), f (Qf x N) and, for Liang2014, phi*u of the
+    """Concatenate g (Qg x N), f (Qf x N) and, for Liang2014/Liang2018, phi*u of the
     previous step (d x N), each cell-major with x fastest."""
     parts = [st.g.reshape(st.g.shape[0], -1), st.f.reshape(st.f.shape[0], -1)]
-    if P["family"] == LIANG2014:
+    if P["family"] in PHIU_FAMILIES:
         parts.append(st.phiu_prev.reshape(P["dim"], -1))
     return np.concatenate(parts, axis=0)
 
@@ -715,6 +757,6 @@ def unpack_state(P, blob, t=0):
     g = blob[: lg.Q].reshape((lg.Q,) + shape).copy()
     f = blob[lg.Q: lg.Q + lf.Q].reshape((lf.Q,) + shape).copy()
     phiu = None
-    if P["family"] == LIANG2014:
+    if P["family"] in PHIU_FAMILIES:
         phiu = blob[lg.Q + lf.Q: lg.Q + lf.Q + P["dim"]].reshape((P["dim"],) + shape).copy()
     return State(g, f, phiu, t)

@@ -15,10 +15,10 @@ import math
 
 import numpy as np
 
-FAKHARI2017, CHAI2018, HU2019, LIANG2014 = 0, 1, 2, 3
-FAMILIES = (FAKHARI2017, CHAI2018, HU2019, LIANG2014)
+FAKHARI2017, CHAI2018, HU2019, LIANG2014, LIANG2018 = 0, 1, 2, 3, 4
+FAMILIES = (FAKHARI2017, CHAI2018, HU2019, LIANG2014, LIANG2018)
 FAMILY_NAMES = {FAKHARI2017: "fakhari2017", CHAI2018: "chai2018",
-                HU2019: "hu2019", LIANG2014: "liang2014"}
+                HU2019: "hu2019", LIANG2014: "liang2014", LIANG2018: "liang2018"}
 
 DEFAULT_SEED = 20251114
 
@@ -295,7 +295,9 @@ def shear_instance(L, family, Ca, M, W, Uw=0.02, tau=0.8):
 
 def batched_shear_sweep(count=512, sizes=(64, 128, 256, 512), seed=DEFAULT_SEED):
     """``count`` instances with L uniform in ``sizes``, Ca ~ U[0.05, 0.5],
-    M ~ U[0.01, 0.2], W uniform in {3, 4, 5}, family uniform over the four."""
+    M ~ U[0.01, 0.2], W uniform in {3, 4, 5}, family uniform over the four
+    families of the paper's model comparison (Fakhari2017, Chai2018, Hu2019,
+    Liang2014)."""
     rng = np.random.default_rng(seed)
     out = []
     for _ in range(count):

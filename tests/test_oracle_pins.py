@@ -231,6 +231,18 @@ def test_source_moments(dim):
     Fl = O.force_liang2014(lf, u, grho, F)
     assert np.allclose(Fl.sum(0), np.sum(u * grho, 0), atol=1e-16)
     assert np.allclose(_mom(lf, Fl, 1), F, atol=1e-16)
+    # Liang2018 force (Eq. liang_F_final, printed /c_s^2): zeroth moment
+    # u.grad(rho), first F, second c_s^2 [(u.grad rho) I + u grad(rho) + grad(rho) u]
+    # (the isotropic fourth moment c_s^4 (d d + d d + d d) of Sec. II B lattices).
+    F8 = O.force_liang2018(lf, u, grho, F)
+    ug = np.sum(u * grho, 0)
+    assert np.allclose(F8.sum(0), ug, atol=1e-16)
+    assert np.allclose(_mom(lf, F8, 1), F, atol=1e-16)
+    sec = _mom(lf, F8, 2)
+    for i in range(dim):
+        for j in range(dim):
+            want = cs2 * ((ug if i == j else 0.0) + u[i] * grho[j] + grho[i] * u[j])
+            assert np.allclose(sec[i, j], want, atol=1e-16)
 
 
 def test_nonlocal_source_sums_to_zero():
