@@ -12,7 +12,8 @@ W = 4, We = 5, density ratio 1, linear forcing, conservative Allen-Cahn
                step's observables, final phi copied back to the host
   roofline     algorithmic bytes/LU x cells / kernel time against the measured
                HBM copy bandwidth
-  variants     FP16 / BF16 deviation storage of the same workload, and the
+  variants     FP16 / BF16 deviation storage of the same workload; the other
+               four families (Chai2018, Hu2019, Liang2014, Liang2018) on it; the
                batched form: 512 2D droplet-in-shear domains (sizes uniform in
                {64,128,256,512}^2, the four families mixed) in one persistent
                launch per step, autotuned launch shape, CUDA-graph replay;
@@ -360,6 +361,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-families", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -423,6 +425,22 @@ def main():
                               "bytes_per_lu": b2, "roofline_frac": b2 * cells / (t2 / args.steps) / 1e9 / peak,
                               "ms_per_step": t2 / args.steps * 1e3}
 
+        if not args.no_families:
+            # The other families on the same workload and storage (the paper's
+            # Table III compares the families' cost on one 3D case).
+            fams = {}
+            for fam in (C.CHAI2018, C.HU2019, C.LIANG2014, C.LIANG2018):
+                s3 = pflb.Sim(dict(P, family=fam, storage=storage, obs_capacity=4),
+                              stream=torch.cuda.current_stream())
+                s3.init(phi, u)
+                b3 = s3.bytes_per_update()
+                t3 = _max_over_ranks(time_steps(s3, args.steps, args.warmup, world), world)
+                s3.close()
+                fams[C.FAMILY_NAMES[fam]] = {
+                    "value": cells * args.steps * world / t3 / 1e9, "unit": "GLUPS", "bytes_per_lu": b3,
+                    "roofline_frac": b3 * cells / (t3 / args.steps) / 1e9 / peak,
+                    "ms_per_step": t3 / args.steps * 1e3, "time_vs_fakhari2017": t3 / t}
+            variants["families_%s" % args.storage] = fams
         if not args.no_batched:
             variants["batched_2d_shear_512"] = batched_variant(args.steps, args.warmup, peak)
         if not args.no_adjoint:

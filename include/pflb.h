@@ -49,12 +49,17 @@ typedef enum pflb_status {
   PFLB_ETIMEOUT = -5   /* a bounded device-side wait expired */
 } pflb_status;
 
-/* Phase-field model family (the four categories of Sec. II C and II D). */
+/* Phase-field model family (the four categories of Sec. II C and II D, and
+ * Liang2018, the second conservative Allen-Cahn model of Sec. II C 2). */
 typedef enum pflb_family {
   PFLB_CAC_FAKHARI2017 = 0, /* conservative Allen-Cahn, Sec. II C 1 */
   PFLB_NLAC_CHAI2018 = 1,   /* nonlocal Allen-Cahn, Sec. II C 3 */
   PFLB_HAC_HU2019 = 2,      /* hybrid Allen-Cahn with global weight lambda, Sec. II C 4 */
-  PFLB_CH_LIANG2014 = 3     /* Cahn-Hilliard with incompressible NS, Sec. II D 1 */
+  PFLB_CH_LIANG2014 = 3,    /* Cahn-Hilliard with incompressible NS, Sec. II D 1 */
+  PFLB_CAC_LIANG2018 = 4    /* conservative Allen-Cahn with the conservative NS form:
+                               first-order g_eq, pressure-based f_eq, d_t(phi u) in G,
+                               Sec. II C 2 (Eqs. liang_geq, liang_feq, liang_G_final,
+                               liang_F_final, liang_velocity_update, liang_p_update) */
 } pflb_family;
 
 /* Population storage in device memory. Arithmetic is always FP32. The 16-bit

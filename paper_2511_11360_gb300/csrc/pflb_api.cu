@@ -70,7 +70,7 @@ int validate(const pflb_params* p, char* msg, size_t n) {
   const long long qmax = p->dim == 2 ? 9 : 19;
   if (((N + 31) / 32) * 32 * qmax >= (1LL << 32))
     return snprintf(msg, n, "Q * cells must be < 2^32 (%lld cells max)", ((1LL << 32) - 1) / qmax / 32 * 32), PFLB_EINVAL;
-  if (p->family < 0 || p->family > 3) return snprintf(msg, n, "unknown family %d", p->family), PFLB_EINVAL;
+  if (p->family < 0 || p->family > 4) return snprintf(msg, n, "unknown family %d", p->family), PFLB_EINVAL;
   if (p->storage < 0 || p->storage > 2) return snprintf(msg, n, "unknown storage %d", p->storage), PFLB_EINVAL;
   if (p->bc_y < 0 || p->bc_y > 2) return snprintf(msg, n, "bc_y must be 0, 1 or 2"), PFLB_EINVAL;
   if (p->bc_y != 0 && p->dim != 2) return snprintf(msg, n, "walls are supported in 2D only"), PFLB_EINVAL;
@@ -145,7 +145,8 @@ void step_launch(int fam, int dim, int storage, const StepArgs& a, cudaStream_t 
     case 0: step_fakhari(dim, storage, a, s); break;
     case 1: step_chai(dim, storage, a, s); break;
     case 2: step_hu(dim, storage, a, s); break;
-    default: step_liang2014(dim, storage, a, s); break;
+    case 3: step_liang2014(dim, storage, a, s); break;
+    default: step_liang2018(dim, storage, a, s); break;
   }
 }
 
@@ -154,7 +155,8 @@ void init_launch(int fam, int dim, int storage, const InitArgs& a, cudaStream_t 
     case 0: init_fakhari(dim, storage, a, s); break;
     case 1: init_chai(dim, storage, a, s); break;
     case 2: init_hu(dim, storage, a, s); break;
-    default: init_liang2014(dim, storage, a, s); break;
+    case 3: init_liang2014(dim, storage, a, s); break;
+    default: init_liang2018(dim, storage, a, s); break;
   }
 }
 
@@ -308,7 +310,7 @@ int pflb_create(const pflb_params* params, void* cuda_stream, pflb_handle** out)
   if ((rc = alloc(&h->g[0], (size_t)h->QG * npad * h->elem + 16))) return rc;
   if ((rc = alloc(&h->g[1], (size_t)h->QG * npad * h->elem + 16))) return rc;
   if ((rc = alloc(&h->f, (size_t)h->QF * npad * h->elem + 16))) return rc;
-  if (h->family == 3 && (rc = alloc((void**)&h->phiu, (size_t)h->dim * h->N * sizeof(float)))) return rc;
+  if (fam_phiu(h->family) && (rc = alloc((void**)&h->phiu, (size_t)h->dim * h->N * sizeof(float)))) return rc;
   if ((rc = alloc((void**)&h->obs, (size_t)(h->obs_cap + 1) * sizeof(DevObs)))) return rc;
   if ((rc = alloc((void**)&h->gamma_acc, 6 * sizeof(double)))) return rc;
   return PFLB_OK;
@@ -443,7 +445,7 @@ int pflb_get_fields(pflb_handle* h, float* phi, float* u, float* p) {
 
 int64_t pflb_state_floats(const pflb_handle* h) {
   if (!h) return -1;
-  return (int64_t)(h->QG + h->QF + (h->family == 3 ? h->dim : 0)) * h->N;
+  return (int64_t)(h->QG + h->QF + (fam_phiu(h->family) ? h->dim : 0)) * h->N;
 }
 
 
@@ -499,7 +501,7 @@ double pflb_bytes_per_update(const pflb_handle* h) {
   // Allen-Cahn families is identically zero and never touched).
   const int qg = (h->dim == 3 && h->family != 3) ? h->QG - 1 : h->QG;
   double b = 2.0 * (qg + h->QF) * (double)h->elem;
-  if (h->family == 3) b += 2.0 * h->dim * 4.0;        // phi*u read + write
+  if (fam_phiu(h->family)) b += 2.0 * h->dim * 4.0;  // phi*u read + write
   if (handle_nonlocal(h)) b += (double)qg * h->elem;         // g read by the gamma reduction
   return b;
 }

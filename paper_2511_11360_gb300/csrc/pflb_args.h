@@ -23,7 +23,7 @@ struct StepArgs {
   const void* g_src;
   void* g_dst;
   void* f;
-  float* phiu;            // Cahn-Hilliard: phi*u of the previous step (d x N), in place
+  float* phiu;            // Liang2014/Liang2018: phi*u of the previous step (d x N), in place
   DevObs* obs_slot;       // accumulate the observables here
   DevObs* obs_zero;       // zero this slot (the next step's), may be null
   const double* gamma_acc;// nonlocal/hybrid: (I1, I2) of this step
@@ -63,7 +63,7 @@ struct CanonArgs {
   float* state;           // canonical FP32 state
   int parity;             // parity of the next step
   int to_canon;           // 1: storage -> state (save); 0: state -> storage (load)
-  int ch;                 // Cahn-Hilliard (phi*u block present, g_0 stored in 3D)
+  int ch;                 // Cahn-Hilliard (g_0 stored in 3D); the phi*u block is present when phiu != null
   long long N;
 };
 
@@ -101,10 +101,12 @@ void step_fakhari(int dim, int storage, const StepArgs& a, cudaStream_t s);
 void step_chai(int dim, int storage, const StepArgs& a, cudaStream_t s);
 void step_hu(int dim, int storage, const StepArgs& a, cudaStream_t s);
 void step_liang2014(int dim, int storage, const StepArgs& a, cudaStream_t s);
+void step_liang2018(int dim, int storage, const StepArgs& a, cudaStream_t s);
 void init_fakhari(int dim, int storage, const InitArgs& a, cudaStream_t s);
 void init_chai(int dim, int storage, const InitArgs& a, cudaStream_t s);
 void init_hu(int dim, int storage, const InitArgs& a, cudaStream_t s);
 void init_liang2014(int dim, int storage, const InitArgs& a, cudaStream_t s);
+void init_liang2018(int dim, int storage, const InitArgs& a, cudaStream_t s);
 // pflb_aux.cu
 void gamma_sums(int dim, int storage, const GammaArgs& a, cudaStream_t s);
 void canon_copy(int dim, int storage, const CanonArgs& a, cudaStream_t s);

@@ -134,7 +134,7 @@ __global__ void canon_kernel(const CanonArgs a) {
       if (a.to_canon) *sp = pop_loadc<T, LF>(fp, q, 0.0f);
       else pop_store<T, LF>(fp, q, *sp, 0.0f);
     }
-    if (a.ch) {
+    if (a.phiu) {
       for (int k = 0; k < DIM; ++k) {
         float* sp = a.state + (long long)(QG + QF + k) * N + idx;
         float* pp = a.phiu + (long long)k * N + idx;

@@ -21,7 +21,7 @@ struct BatchGeom {
 
 template <int TA>
 __global__ void __launch_bounds__(TA, BatchGeom<TA>::MINB) batch_step_kernel(const BatchArgs ba) {
-  using SMX = TileSmem<FAM_LIANG, 2, float, TA, 1>;  // the largest footprint of the four families
+  using SMX = TileSmem<FAM_LIANG, 2, float, TA, 1>;  // the largest footprint of the families
   extern __shared__ __align__(16) float dyn_smem[];
   float* s_stage = dyn_smem;
   float* s_phi = dyn_smem + SMX::STAGE;
@@ -77,8 +77,14 @@ __global__ void __launch_bounds__(TA, BatchGeom<TA>::MINB) batch_step_kernel(con
       case 2 * FAM_LIANG + 1:
         step_tile<FAM_LIANG, 2, float, TA, 1, -1, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
         break;
-      default:
+      case 2 * FAM_LIANG:
         step_tile<FAM_LIANG, 2, float, TA, 1, -1, 0>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
+        break;
+      case 2 * FAM_LIANG18 + 1:
+        step_tile<FAM_LIANG18, 2, float, TA, 1, -1, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
+        break;
+      default:
+        step_tile<FAM_LIANG18, 2, float, TA, 1, -1, 0>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
         break;
     }
     obs_block_commit(obs, s_args.obs_slot, s_red);

@@ -7,12 +7,19 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace pflb {
 
 constexpr int FAM_FAKHARI = 0;
 constexpr int FAM_CHAI = 1;
 constexpr int FAM_HU = 2;
-constexpr int FAM_LIANG = 3;
+constexpr int FAM_LIANG = 3;     // Liang2014 (Cahn-Hilliard)
+constexpr int FAM_LIANG18 = 4;   // Liang2018 (conservative Allen-Cahn, conservative NS form)
+
+// Families that keep phi*u of the previous step for d_t(phi u) (Sec. III B)
+// and use the pressure-based hydrodynamic equilibrium (Eq. liang2_feq).
+__host__ __device__ constexpr bool fam_phiu(int fam) { return fam == FAM_LIANG || fam == FAM_LIANG18; }
 
 // ---------------------------------------------------------------------------
 // Lattices (c_s^2 = 1/3 for all three, Sec. III and Sec. IV), in the
@@ -226,7 +233,24 @@ __device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+// The same copy with both addresses given as a register plus a compile-time
+// byte offset ([reg+imm] operands), so a run of copies from one cell's
+// populations to one thread's slots needs no address arithmetic per copy.
+template <int SOFF, long long GOFF>
+__device__ __forceinline__ void cp_async4_at(unsigned sbase, const void* gbase) {
+  asm volatile("cp.async.ca.shared.global [%0+%2], [%1+%3], 4;\n" ::"r"(sbase), "l"(gbase), "n"(SOFF), "n"(GOFF)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+// Compile-time loop: fn(std::integral_constant<int, I>) for I in [B, E).
+template <int B, int E, typename Fn>
+__device__ __forceinline__ void static_for(Fn&& fn) {
+  if constexpr (B < E) {
+    fn(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(fn);
+  }
+}
 template <int PENDING>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");

@@ -7,7 +7,7 @@ namespace pflb {
 
 // One thread per cell (grid-stride). g goes to the source array in the
 // canonical slot order; f goes to the AA array in the even-step layout
-// (slot q of the cell holds f_q); Cahn-Hilliard also stores phi*u.
+// (slot q of the cell holds f_q); Liang2014 and Liang2018 also store phi*u.
 template <int FAM, int DIM, typename T>
 __global__ void init_kernel(const InitArgs args) {
   using LG = typename Lattices<DIM>::G;
@@ -69,13 +69,13 @@ __global__ void init_kernel(const InitArgs args) {
       for (int k = 0; k < DIM; ++k) eu += (float)ecomp<LF>(q, k) * u[k];
       const float w = LF::w(q);
       float feq;
-      if constexpr (FAM == FAM_LIANG)
+      if constexpr (fam_phiu(FAM))   // pressure-based f_eq with p = 0 (Eqs. liang_feq, liang2_feq)
         feq = (q == 0) ? rho * w * (-1.5f * usq) : rho * w * (3.0f * eu + 4.5f * eu * eu - 1.5f * usq);
       else
         feq = w * (3.0f * eu + 4.5f * eu * eu - 1.5f * usq);
       pop_store<T, LF>(f + pop_ix<LF>(q, (unsigned)idx), q, feq, 0.0f);
     }
-    if constexpr (FAM == FAM_LIANG) {
+    if constexpr (fam_phiu(FAM)) {
 #pragma unroll
       for (int k = 0; k < DIM; ++k) args.phiu[(long long)k * N + idx] = phi * u[k];
     }

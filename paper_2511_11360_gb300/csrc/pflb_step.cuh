@@ -123,7 +123,16 @@ struct Cell {
     const float A = P.lundA;
     float F[DIM];
 
-    if constexpr (FAM != FAM_LIANG) {
+    if constexpr (FAM == FAM_LIANG18) {
+      // Liang2018: rho u = sum e f + F/2 with F = F_s + F_b (Eq.
+      // liang_velocity_update); the linear forcing A rho u is solved for.
+      const float den = inv_rho / (1.0f - 0.5f * A);
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        u[k] = (mom[k] + 0.5f * (Fs[k] + Fb[k])) * den;
+        F[k] = Fs[k] + Fb[k] + A * rho * u[k];
+      }
+    } else if constexpr (FAM != FAM_LIANG) {
       // Pressure p = rho c_s^2 sum f (Eq. fakhari_p_update); F_p = -(p/rho) grad rho.
       p = rho * cs2 * sumf;
       float Fo[DIM];
@@ -207,7 +216,7 @@ struct Cell {
       geq[0] = phi - Sym<LG>::moving(geq);   // = phi + (w_0 - 1) eta mu
     } else {
       float flux[DIM];
-      bool has_cons = (FAM == FAM_FAKHARI || FAM == FAM_HU);
+      constexpr bool has_cons = (FAM == FAM_FAKHARI || FAM == FAM_HU || FAM == FAM_LIANG18);
       if (has_cons) {
         // Conservative counter term, Eq. (fakhari_G_modified), with the
         // normal regularised as grad phi / sqrt(|grad phi|^2 + eps^2) (R6).
@@ -217,6 +226,16 @@ struct Cell {
         const float sc = P.counter_k * (P.phiH - phi) * (phi - P.phiL) * rsqrtf(g2 + P.eps2);
 #pragma unroll
         for (int k = 0; k < DIM; ++k) flux[k] = sc * gp[k];
+      }
+      // Liang2018: backward-Euler d_t(phi u) (Sec. III B) for Eq. (liang_G_final).
+      float dpu[DIM];
+      if constexpr (FAM == FAM_LIANG18) {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+          const float pu = phi * u[k];
+          dpu[k] = pu - phiu[k];
+          phiu[k] = pu;
+        }
       }
       float Rw = 0.0f, lam = 1.0f;
       if constexpr (FAM == FAM_CHAI || FAM == FAM_HU) {
@@ -232,13 +251,14 @@ struct Cell {
         for (int k = 0; k < DIM; ++k)
           if (ecomp<LG>(q, k) != 0) {
             eu += (float)ecomp<LG>(q, k) * u[k];
-            if (has_cons) ef += (float)ecomp<LG>(q, k) * flux[k];
+            if constexpr (has_cons) ef += (float)ecomp<LG>(q, k) * flux[k];
+            if constexpr (FAM == FAM_LIANG18) ef += (float)ecomp<LG>(q, k) * (3.0f * dpu[k]);
           }
         if constexpr (FAM == FAM_FAKHARI)
           geq[q] = wmul<LG>(q, phi * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * usq));  // Eq. (fakhari_geq)
         else
-          geq[q] = wmul<LG>(q, phi * (1.0f + 3.0f * eu));                               // Eq. (Chai_geq)
-        if constexpr (FAM == FAM_FAKHARI) G[q] = wmul<LG>(q, ef);
+          geq[q] = wmul<LG>(q, phi * (1.0f + 3.0f * eu));                   // Eqs. (Chai_geq), (liang_geq)
+        if constexpr (FAM == FAM_FAKHARI || FAM == FAM_LIANG18) G[q] = wmul<LG>(q, ef);  // Eq. (liang_G_final)
         else if constexpr (FAM == FAM_CHAI) G[q] = wmul<LG>(q, Rw);
         else G[q] = wmul<LG>(q, lam * ef + Rw);                                        // Eq. (Hu_G)
       }
@@ -251,9 +271,10 @@ struct Cell {
     for (int q = 0; q < QG; ++q) g[q] = g[q] - (g[q] - geq[q]) * P.inv_tau_phi + P.src_w_phi * G[q];
 
     // ---------------- hydrodynamics ----------------
-    if constexpr (FAM == FAM_LIANG) {
-      // p by Eq. (liang_p_update); pressure-based f_eq and forcing of Eqs.
-      // (liang2_feq), (liang2_F), (Gamma_beta).
+    if constexpr (fam_phiu(FAM)) {
+      // p by Eq. (liang_p_update); pressure-based f_eq (Eqs. liang2_feq,
+      // liang_feq) and forcing of Eqs. (liang2_F), (Gamma_beta) for Liang2014,
+      // of Eq. (liang_F_final) for Liang2018.
       float udg = 0.0f;
 #pragma unroll
       for (int k = 0; k < DIM; ++k) udg += u[k] * grho[k];
@@ -283,15 +304,26 @@ struct Cell {
         const float Gam = wmul<LF>(q, 3.0f * eu + 4.5f * eu * eu - 1.5f * usq);
         const float feq = (q == 0) ? wmul<LF>(q, p3) - p3 + wmul<LF>(q, rho * (-1.5f * usq))
                                    : wmul<LF>(q, p3) + rho * Gam;
-        const float Fq = 3.0f * ((ea - ua) * Gam + (eF - uF) * Gam + wmul<LF>(q, eF - uF));
+        float Fq;
+        if constexpr (FAM == FAM_LIANG)
+          Fq = 3.0f * ((ea - ua) * Gam + (eF - uF) * Gam + wmul<LF>(q, eF - uF));
+        else
+          // w [u.grad rho + 3 e.F + 3 ((e.u)(e.grad rho) - c_s^2 u.grad rho)]: the
+          // u.grad rho terms cancel, leaving w (3 e.F + 3 (e.u)(e.grad rho)),
+          // with ea = c_s^2 e.grad rho.
+          Fq = wmul<LF>(q, 3.0f * eF + 9.0f * eu * ea);
         f[q] = f[q] - (f[q] - feq) * itau + fw * Fq;
       }
     } else {
       // f* = f - (f - f_eq) itau + fw F_b = f (1 - itau) + w (itau X + fw Y), with
       // f_eq = w X, X = sum f + 3 e.u + 4.5 (e.u)^2 - 1.5 u.u   Eq. (fakhari_feq),
       // F_b = w Y, Y = 3 e.F~ (Eq. fakhari_F) or
-      //       3 e.F~ + 9 (e.u)(e.F~) - 3 u.F~ (Eq. chai_F, Reading R2), F~ = F/rho;
-      // one weight product per velocity.
+      //       3 e.F~ + 9 (e.u)(e.F~) - 3 u.F~ (Eq. chai_F, Reading R2), F~ = F/rho.
+      // A velocity and its opposite share everything but the sign of e: with
+      // e.u and e.F~ of the first, itau X + fw Y = E + O for it and E - O for
+      // the opposite, E = itau (sum f - 1.5 u.u + 4.5 (e.u)^2) + fw Y_even,
+      // O = 3 (itau e.u + fw e.F~). Every operation is sign-symmetric, so the
+      // mirror image of a cell still gets the mirror image of its update.
       float Ft[DIM], uFt = 0.0f;
 #pragma unroll
       for (int k = 0; k < DIM; ++k) {
@@ -300,8 +332,13 @@ struct Cell {
       }
       const float s0 = sumf - 1.5f * usq;
       const float omi = 1.0f - itau;
+      const float itau3 = 3.0f * itau, fw3 = 3.0f * fw;
+      const float ye0 = (FAM == FAM_FAKHARI) ? 0.0f : -3.0f * uFt;   // even part of Y at e = 0
+      f[0] = fmaf(f[0], omi, wmul<LF>(0, fmaf(itau, s0, fw * ye0)));
 #pragma unroll
-      for (int q = 0; q < QF; ++q) {
+      for (int q = 1; q < QF; ++q) {
+        const int qo = LF::opp(q);
+        if (qo < q) continue;   // each pair once, from its first member
         float eu = 0.0f, eF = 0.0f;
 #pragma unroll
         for (int k = 0; k < DIM; ++k)
@@ -310,11 +347,12 @@ struct Cell {
             eu += e * u[k];
             eF += e * Ft[k];
           }
-        const float X = fmaf(eu, fmaf(4.5f, eu, 3.0f), s0);
-        float Y;
-        if constexpr (FAM == FAM_FAKHARI) Y = 3.0f * eF;
-        else Y = fmaf(9.0f * eu, eF, 3.0f * (eF - uFt));
-        f[q] = fmaf(f[q], omi, wmul<LF>(q, fmaf(itau, X, fw * Y)));
+        float E;
+        if constexpr (FAM == FAM_FAKHARI) E = itau * fmaf(4.5f * eu, eu, s0);
+        else E = fmaf(itau, fmaf(4.5f * eu, eu, s0), fw * fmaf(9.0f * eu, eF, ye0));
+        const float O = fmaf(itau3, eu, fw3 * eF);
+        f[q] = fmaf(f[q], omi, wmul<LF>(q, E + O));
+        f[qo] = fmaf(f[qo], omi, wmul<LF>(qo, E - O));
       }
     }
   }
@@ -388,7 +426,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
   const int tid = tx + TA * ty;
   const int a = a0 + tx, b = b0 + ty;
   const bool active = (a < NA) && (b < NB);
-  const bool walls = P.walls != 0;
+  const bool walls = DIM == 2 && P.walls != 0;   // walls are a 2D feature
   // AA parity of this step: a compile-time constant for the single-domain
   // kernel (one instantiation per parity), read from the arguments otherwise.
   const int parity = PAR >= 0 ? PAR : args.parity;
@@ -519,14 +557,16 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
   auto A_of = [&](int d) { return d < 0 ? am : (d > 0 ? ap : aw); };
   auto RB_of = [&](int d) { return d < 0 ? rbm : (d > 0 ? rbp : rbw); };
 
-  // Element offsets in the block layout (pop_ix). When nx is a multiple of
-  // the block width, shifting a cell by whole rows or planes moves each of
-  // its populations by a multiple of the block stride, so the offset of
-  // population q of the neighbour (x + da, y + db) on plane cs is
-  //   E0 + D_x(da) + D_y(db) + cs * Q * nx * ny + 32 q
-  // with per-thread constants E0, D_x, D_y (periodic wrap included) and the
-  // velocity's part an immediate. Otherwise the cell index is formed and
-  // mapped (pop_ix) per access.
+  // Element offsets in the block layout (pop_ix): population q of a cell
+  // sits 32 q elements after its population 0, so every access below forms
+  // one pointer per cell (population 0) and reaches the populations by
+  // compile-time offsets. When nx is a multiple of the block width, shifting
+  // a cell by whole rows or planes moves its population 0 by a multiple of
+  // the block stride, so the population-0 offset of the neighbour
+  // (x + da, y + db) on plane cs is
+  //   E0 + D_x(da) + D_y(db) + cs * Q * nx * ny
+  // with per-thread constants E0, D_x, D_y (periodic wrap included).
+  // Otherwise the cell index is formed and mapped (pop_ix) per cell.
   // ROW: 1 = nx is a multiple of the block width, 0 = it is not, -1 = test here.
   const bool rowal = ROW >= 0 ? ROW == 1 : (NA % (int)kPopBlock) == 0;
   const unsigned cell0 = (unsigned)(aw + rbw);
@@ -536,42 +576,36 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
   const unsigned gdxm = pop_ix<LG>(0, (unsigned)(am + rbw)) - gE0, gdxp = pop_ix<LG>(0, (unsigned)(ap + rbw)) - gE0;
   const unsigned gdym = pop_ix<LG>(0, (unsigned)(aw + rbm)) - gE0, gdyp = pop_ix<LG>(0, (unsigned)(aw + rbp)) - gE0;
   const unsigned fplane = (unsigned)NAB * (unsigned)QF, gplane = (unsigned)NAB * (unsigned)QG;
-  // Population q of the cell (x + da, y + db) on plane cs (cs already wrapped).
-  auto f_at = [&](int q, int da, int db, int cs) -> unsigned {
+  // Population 0 of the cell (x + da, y + db) on plane cs (cs already wrapped).
+  auto f_cell = [&](int da, int db, int cs) -> unsigned {
     if (rowal)
       return fE0 + (da < 0 ? fdxm : (da > 0 ? fdxp : 0u)) + (db < 0 ? fdym : (db > 0 ? fdyp : 0u)) +
-             (unsigned)cs * fplane + (unsigned)q * kPopBlock;
-    return pop_ix<LF>(q, (unsigned)(A_of(da) + RB_of(db) + cs * NAB));
+             (unsigned)cs * fplane;
+    return pop_ix<LF>(0, (unsigned)(A_of(da) + RB_of(db) + cs * NAB));
   };
-  auto g_at = [&](int q, int da, int db, int cs) -> unsigned {
+  auto g_cell = [&](int da, int db, int cs) -> unsigned {
     if (rowal)
       return gE0 + (da < 0 ? gdxm : (da > 0 ? gdxp : 0u)) + (db < 0 ? gdym : (db > 0 ? gdyp : 0u)) +
-             (unsigned)cs * gplane + (unsigned)q * kPopBlock;
-    return pop_ix<LG>(q, (unsigned)(A_of(da) + RB_of(db) + cs * NAB));
+             (unsigned)cs * gplane;
+    return pop_ix<LG>(0, (unsigned)(A_of(da) + RB_of(db) + cs * NAB));
   };
   // Plane reached from c by dc (periodic, or c itself at a wall).
   auto plane_of = [&](int c, int dc) -> int {
     return dc < 0 ? (c == 0 ? NC - 1 : c - 1) : (dc > 0 ? (c == NC - 1 ? 0 : c + 1) : c);
   };
-
-  // Element offset of the f population q the own cell reads at plane c (AA
-  // pattern): even steps its own slot q; odd steps slot opp(q) of x - e_q,
-  // or its own slot q where x - e_q lies beyond a wall.
-  auto f_read_ofs = [&](int c, int q) -> unsigned {
-    const int da = da_of<DIM, LF>(q), db = db_of<DIM, LF>(q), dc = dc_of<DIM, LF>(q);
-    const bool cross = walls && ((dc > 0 && c == 0) || (dc < 0 && c == NC - 1));
-    if (parity == 0 || cross) return f_at(q, 0, 0, c);
-    return f_at(LF::opp(q), -da, -db, plane_of(c, -dc));
-  };
-  // Own and halo g of plane cg: the halo cells' offsets relative to their
-  // plane are per-thread constants in the row-aligned case.
+  // AA pattern, f population q the own cell reads at plane c: even steps its
+  // own slot q; odd steps slot opp(q) of x - e_q, or its own slot q where
+  // x - e_q lies beyond a wall.
+  auto f_read_crosses = [&](int c, int dc) { return walls && ((dc > 0 && c == 0) || (dc < 0 && c == NC - 1)); };
+  // Own and halo g of plane cm (mapped): the halo cells' offsets relative to
+  // their plane are per-thread constants in the row-aligned case.
   unsigned gHalo0[KH];
 #pragma unroll
   for (int k = 0; k < KH; ++k) gHalo0[k] = pop_ix<LG>(0, (unsigned)halo_ab[k]);
   const unsigned gOwn0 = pop_ix<LG>(0, (unsigned)own_ab);
-  auto g_src_ofs = [&](int q, int k, int cm) -> unsigned {   // k < 0: own cell; cm: mapped plane
-    if (rowal) return (k < 0 ? gOwn0 : gHalo0[k]) + (unsigned)cm * gplane + (unsigned)q * kPopBlock;
-    return pop_ix<LG>(q, (unsigned)((k < 0 ? own_ab : halo_ab[k]) + NAB * cm));
+  auto g_src_cell = [&](int k, int cm) -> unsigned {   // k < 0: own cell
+    if (rowal) return (k < 0 ? gOwn0 : gHalo0[k]) + (unsigned)cm * gplane;
+    return pop_ix<LG>(0, (unsigned)((k < 0 ? own_ab : halo_ab[k]) + NAB * cm));
   };
 
   // The incoming g of plane cg (own cell and this thread's halo cells) and
@@ -582,41 +616,66 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
   // at least 4 aligned bytes: a 16-bit population is fetched as the aligned
   // word that contains it (its neighbour's half is ignored; the arrays are
   // allocated with padding so the last word is in bounds), and a bit of
-  // gm/fm records which half is ours.
+  // gm/fm records which half is ours. Populations of one cell are 32
+  // elements apart, an even count, so they all sit in the same half.
   constexpr bool WIDE = sizeof(T) == 4;
+  constexpr long long TSZ = (long long)sizeof(T);
+  constexpr long long PSTRIDE = (long long)kPopBlock * TSZ;   // bytes between populations of a cell
   static_assert((1 + KH) * QG <= 32, "half-select bits of the staged g");
   auto stage_f = [&](int s) { return s_stage + s * (FST + GST); };
   auto stage_g = [&](int s) { return s_stage + s * (FST + GST) + FST; };
-  auto word_of = [&](const T* base, unsigned e, unsigned& bits, int bit) -> const float* {
+  const unsigned s_stage_u32 = (unsigned)__cvta_generic_to_shared(s_stage);
+  // Address of the aligned word holding element e of base; its half in hb.
+  auto word_at = [&](const T* base, unsigned e, unsigned& hb) -> const void* {
     if constexpr (WIDE) {
-      (void)bits;
-      (void)bit;
-      return reinterpret_cast<const float*>(base + e);
+      hb = 0u;
+      return base + e;
     } else {
-      bits |= (e & 1u) << bit;
-      return reinterpret_cast<const float*>(base + (e & ~1u));
+      hb = e & 1u;
+      return base + (e & ~1u);
     }
   };
   auto issue = [&](int cg, int cf, int s, unsigned& gm, unsigned& fm) {
-    float* gs = stage_g(s);
     gm = 0u;
     fm = 0u;
     const int cm = map_c(cg);
-#pragma unroll
-    for (int q = SKIP0 ? 1 : 0; q < QG; ++q)
-      cp_async4(gs + q * PLANE + tid, word_of(gsrc, g_src_ofs(q, -1, cm), gm, q));
-#pragma unroll
-    for (int k = 0; k < KH; ++k) {
-      if (halo_pos[k] >= 0) {
-#pragma unroll
-        for (int q = SKIP0 ? 1 : 0; q < QG; ++q)
-          cp_async4(gs + q * PLANE + NT + tid + k * NT, word_of(gsrc, g_src_ofs(q, k, cm), gm, (1 + k) * QG + q));
-      }
+    const unsigned sg = s_stage_u32 + (unsigned)(s * (FST + GST) + FST + tid) * 4u;
+    {
+      unsigned hb;
+      const void* w = word_at(gsrc, g_src_cell(-1, cm), hb);
+      static_for<SKIP0 ? 1 : 0, QG>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        cp_async4_at<q * PLANE * 4, q * PSTRIDE>(sg, w);
+        gm |= hb << q;
+      });
     }
+    static_for<0, KH>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      if (halo_pos[k] >= 0) {
+        unsigned hb;
+        const void* w = word_at(gsrc, g_src_cell(k, cm), hb);
+        static_for<SKIP0 ? 1 : 0, QG>([&](auto qc) {
+          constexpr int q = decltype(qc)::value;
+          cp_async4_at<(q * PLANE + NT + k * NT) * 4, q * PSTRIDE>(sg, w);
+          gm |= hb << ((1 + k) * QG + q);
+        });
+      }
+    });
     if (active) {
-      float* fs = stage_f(s);
-#pragma unroll
-      for (int q = 0; q < QF; ++q) cp_async4(fs + q * NT + tid, word_of(fb, f_read_ofs(cf, q), fm, q));
+      const unsigned sf = s_stage_u32 + (unsigned)(s * (FST + GST) + tid) * 4u;
+      static_for<0, QF>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        constexpr int da = da_of<DIM, LF>(q), db = db_of<DIM, LF>(q), dc = dc_of<DIM, LF>(q);
+        unsigned hb;
+        if (parity == 0 || f_read_crosses(cf, dc)) {
+          const void* w = word_at(fb, f_cell(0, 0, cf), hb);
+          cp_async4_at<q * NT * 4, q * PSTRIDE>(sf, w);
+        } else {
+          const void* w = word_at(fb, f_cell(-da, -db, plane_of(cf, -dc)), hb);
+          cp_async4_at<q * NT * 4, LF::opp(q) * PSTRIDE>(sf, w);
+        }
+        fm |= hb << q;
+      });
     }
   };
   // Decode one staged population.
@@ -740,10 +799,16 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
         for (int q = 0; q < QF; ++q) f[q] = staged(fs[q * NT + tid], fms, q, q, false);
       } else {
 #pragma unroll
-        for (int q = 0; q < QF; ++q) f[q] = pop_loadc<T, LF>(fb + f_read_ofs(c, q), q, 0.0f);
+        for (int q = 0; q < QF; ++q) {
+          const int da = da_of<DIM, LF>(q), db = db_of<DIM, LF>(q), dc = dc_of<DIM, LF>(q);
+          const T* src = (parity == 0 || f_read_crosses(c, dc))
+                             ? fb + f_cell(0, 0, c) + q * kPopBlock
+                             : fb + f_cell(-da, -db, plane_of(c, -dc)) + LF::opp(q) * kPopBlock;
+          f[q] = pop_loadc<T, LF>(src, q, 0.0f);
+        }
       }
       float phiu[DIM];
-      if constexpr (CH) {
+      if constexpr (fam_phiu(FAM)) {
 #pragma unroll
         for (int k = 0; k < DIM; ++k) phiu[k] = args.phiu[k * N + idx];
       }
@@ -781,7 +846,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
         for (int k = 0; k < DIM; ++k) args.out_u[k * N + idx] = u[k];
         args.out_p[idx] = p;
       } else {
-        if constexpr (CH) {
+        if constexpr (fam_phiu(FAM)) {
 #pragma unroll
           for (int k = 0; k < DIM; ++k) args.phiu[k * N + idx] = phiu[k];
         }
@@ -792,17 +857,17 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
           if (DIM == 3 && !CH && q == 0) continue;
           const int da = da_of<DIM, LG>(q), db = db_of<DIM, LG>(q), dc = dc_of<DIM, LG>(q);
           if (P.freeze) {
-            pop_store<T, LG>(gdst + g_at(q, 0, 0, c), q, g0[q], P.gref);
+            pop_store<T, LG>(gdst + g_cell(0, 0, c) + q * kPopBlock, q, g0[q], P.gref);
           } else if (crosses(dc)) {
             const float uw = dc < 0 ? uw_lo : uw_hi;
             const float v = gnew[q] - 6.0f * LG::w(q) * pc * (float)LG::ex(q) * uw;
-            pop_store<T, LG>(gdst + g_at(LG::opp(q), 0, 0, c), q, v, P.gref);
+            pop_store<T, LG>(gdst + g_cell(0, 0, c) + LG::opp(q) * kPopBlock, q, v, P.gref);
           } else {
-            pop_store<T, LG>(gdst + g_at(q, da, db, plane_of(c, dc)), q, gnew[q], P.gref);
+            pop_store<T, LG>(gdst + g_cell(da, db, plane_of(c, dc)) + q * kPopBlock, q, gnew[q], P.gref);
           }
         }
         // f: AA pattern.
-        const float sc = CH ? rho : 1.0f;
+        const float sc = fam_phiu(FAM) ? rho : 1.0f;   // first-order f_eq scale: rho for the pressure-based forms
 #pragma unroll
         for (int q = 0; q < QF; ++q) {
           const int da = da_of<DIM, LF>(q), db = db_of<DIM, LF>(q), dc = dc_of<DIM, LF>(q);
@@ -813,9 +878,9 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
             v -= 6.0f * LF::w(q) * sc * (float)LF::ex(q) * uw;
           }
           if (parity == 0 || cr) {
-            pop_store<T, LF>(fb + f_at(LF::opp(q), 0, 0, c), q, v, 0.0f);
+            pop_store<T, LF>(fb + f_cell(0, 0, c) + LF::opp(q) * kPopBlock, q, v, 0.0f);
           } else {
-            pop_store<T, LF>(fb + f_at(q, da, db, plane_of(c, dc)), q, v, 0.0f);
+            pop_store<T, LF>(fb + f_cell(da, db, plane_of(c, dc)) + q * kPopBlock, q, v, 0.0f);
           }
         }
       }

@@ -34,17 +34,17 @@ def _gpu():
 
 
 def mixed_domains():
-    """Eight domains: each family on a ragged periodic grid (a droplet in a
-    vortex, density ratio 2 on half of them) and in a moving-wall channel."""
+    """Ten domains: each family on a ragged periodic grid (a droplet in a
+    vortex, density ratio 2 on three of them) and in a moving-wall channel."""
     out = []
-    sizes = [(150, 37), (70, 53), (97, 40), (200, 29)]
+    sizes = [(150, 37), (70, 53), (97, 40), (200, 29), (120, 45)]
     for k, fam in enumerate(C.FAMILIES):
         nx, ny = sizes[k]
         P, phi, u = C.droplet_in_vortex_2d(nx=nx, ny=ny, R=9.0, W=4.0, family=fam)
         if k % 2 == 0:
             P.update(rho_H=2.0, rho_L=1.0, nu_L=0.05)
         out.append((P, phi, u))
-        L = (36, 64, 48, 72)[k]
+        L = (36, 64, 48, 72, 56)[k]
         out.append(C.shear_instance(L, fam, Ca=0.1 + 0.1 * k, M=0.02 + 0.03 * k, W=3 + k % 3))
     return out
 

@@ -1,7 +1,7 @@
 """Parity at the full sizes of the benchmark workloads, in the launch
 configuration the benchmark uses (default block chunking).
 
-  * 2D Rayleigh-Taylor, 256 x 1024, walls, Atwood 0.5, all four families:
+  * 2D Rayleigh-Taylor, 256 x 1024, walls, Atwood 0.5, all five families:
     whole-field comparison with the FP64 oracle after 50 steps (an unstable
     flow: the bound widens to 3x the oracle's own sensitivity if needed).
   * 3D droplet-laden turbulence, 512^3, 200 droplets, Fakhari2017, FP32 and

@@ -4,7 +4,7 @@ Bars (Reading R15 metric, max|a - b| / max|b|):
   * one step from the same canonical state: populations within FP32 round-off
     (FP16/BF16 storage: within the 16-bit encoding of the written deviation);
   * 1000 steps on laminar cases, ragged grids spanning several tiles and
-    chunks, all four families, periodic / resting walls / moving walls / 3D:
+    chunks, all five families, periodic / resting walls / moving walls / 3D:
     phi and u within 1e-5 -- or, where the FP32 floor of the model on that
     case is higher (rounding repeats coherently in quasi-steady flow), within
     3x the deviation of the same equations evaluated in FP32 by the oracle,
@@ -286,7 +286,7 @@ def _mirror_state(P, blob, axis):
     return O.pack_state(P, O.State(refl(lg, st.g), refl(lf, st.f), phiu)).reshape(-1).astype(np.float32)
 
 
-@pytest.mark.parametrize("fam", [C.FAKHARI2017, C.LIANG2014], ids=["fakhari2017", "liang2014"])
+@pytest.mark.parametrize("fam", [C.FAKHARI2017, C.LIANG2014, C.LIANG2018], ids=["fakhari2017", "liang2014", "liang2018"])
 @pytest.mark.parametrize("kind,axis", [("2d", 0), ("2d_walls", 0), ("2d_walls", 1), ("3d", 0), ("3d", 2)])
 def test_step_is_mirror_exact(fam, kind, axis):
     """The FP32 step commutes bit for bit with reflections of the domain: every
