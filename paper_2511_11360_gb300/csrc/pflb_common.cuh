@@ -241,6 +241,10 @@ __device__ __forceinline__ void cp_async4_at(unsigned sbase, const void* gbase) 
   asm volatile("cp.async.ca.shared.global [%0+%2], [%1+%3], 4;\n" ::"r"(sbase), "l"(gbase), "n"(SOFF), "n"(GOFF)
                : "memory");
 }
+// 16-byte global -> shared copy cached in L2 only (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(unsigned saddr, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 
 // Compile-time loop: fn(std::integral_constant<int, I>) for I in [B, E).

@@ -358,10 +358,19 @@ struct Cell {
   }
 };
 
+// Number of 16-byte f chunks a block stages per plane (cooperative staging):
+// per velocity and tile row TA / CE chunks, one more on odd steps where e_x != 0.
+template <typename LF, int PAR, int TB, int NCH0>
+__host__ __device__ constexpr int coop_items() {
+  int n = 0;
+  for (int q = 0; q < LF::Q; ++q) n += TB * (NCH0 + ((PAR == 1 && LF::ex(q) != 0) ? 1 : 0));
+  return n;
+}
+
 // ---------------------------------------------------------------------------
 // Shared-memory footprint of one tile march.
 // ---------------------------------------------------------------------------
-template <int FAM, int DIM, typename T, int TA, int TB>
+template <int FAM, int DIM, typename T, int TA, int TB, bool COOP = false>
 struct TileSmem {
   static constexpr bool CH = (FAM == FAM_LIANG);
   static constexpr int H = CH ? 2 : 1;
@@ -372,13 +381,22 @@ struct TileSmem {
   static constexpr int PHI = NSLOT * PLANE;
   static constexpr int MU = CH ? 4 * (TA + 2) * (TB + 2 * ((DIM == 3) ? 1 : 0)) : 1;
   // The populations of the next planes are staged asynchronously: NST stages
-  // of f (Q_f words per cell) and g (Q_g words per cell of the tile and
-  // halo); a 16-bit population is staged as the aligned 32-bit word holding it.
+  // of f and g (Q_g words per cell of the tile and halo); a 16-bit g is
+  // staged as the aligned 32-bit word holding it. f is staged either per
+  // thread (Q_f words per cell) or, with COOP, by the whole block in 16-byte
+  // chunks: per velocity and tile row, TA + CE elements of the storage type
+  // (CE = 16 bytes of elements; the extra chunk holds the neighbour cell an
+  // odd AA step reads across the tile's x edge).
   static constexpr bool STAGED = true;
-  static constexpr int FST = Lattices<DIM>::F::Q * NT;
+  static constexpr int CE = 16 / (int)sizeof(T);
+  static constexpr int FROW = TA + CE;
+  static constexpr int FST = COOP ? Lattices<DIM>::F::Q * TB * FROW * (int)sizeof(T) / 4 : Lattices<DIM>::F::Q * NT;
   static constexpr int GST = Lattices<DIM>::G::Q * PLANE;
-  static constexpr int NST = 3;   // stages: plane c is consumed while c+1, c+2 are in flight
+  // COOP refills a stage only after the next plane's barrier, so it keeps one
+  // stage more in flight (Cahn-Hilliard tiles have no room for it).
+  static constexpr int NST = (COOP && !CH) ? 4 : 3;
   static constexpr int STAGE = STAGED ? NST * (FST + GST) : 0;
+  static_assert(!COOP || (FST % 4 == 0 && GST % 4 == 0), "16-byte aligned stages");
   static constexpr size_t BYTES = (size_t)(STAGE + PHI + MU) * sizeof(float);
 };
 
@@ -409,9 +427,14 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
   constexpr int MSLOT = 4;
   constexpr int MHALO = MPLANE - NT;
   constexpr int KM = (MHALO + NT - 1) / NT;
-  constexpr bool STAGED = TileSmem<FAM, DIM, T, TA, TB>::STAGED;
-  constexpr int FST = TileSmem<FAM, DIM, T, TA, TB>::FST, GST = TileSmem<FAM, DIM, T, TA, TB>::GST;
-  constexpr int NST = TileSmem<FAM, DIM, T, TA, TB>::NST;
+  // COOP: the block stages f together in 16-byte chunks (3D, rows aligned to
+  // the population blocks, AA parity known at compile time).
+  constexpr bool COOP = (DIM == 3) && (ROW == 1) && (PAR >= 0);
+  using SMEM = TileSmem<FAM, DIM, T, TA, TB, COOP>;
+  constexpr bool STAGED = SMEM::STAGED;
+  constexpr int FST = SMEM::FST, GST = SMEM::GST;
+  constexpr int NST = SMEM::NST;
+  constexpr int CE = SMEM::CE, FROW = SMEM::FROW;
   constexpr bool SKIP0 = (DIM == 3 && !CH);   // D3Q7 rest slot of the AC families: w_0 = 0, g_0 = 0
   (void)RB;
 
@@ -635,6 +658,46 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
       return base + (e & ~1u);
     }
   };
+  // COOP f items: the stage of one plane is QF x TB rows of FROW elements;
+  // row (q, r) holds the slot f reads for velocity q on tile row r, chunk j
+  // (CE elements) at element CE j. Even steps read the own cells (slot q);
+  // odd steps slot opp(q) of x - e_q, so a velocity with e_x != 0 needs one
+  // cell beyond the tile: for e_x = +1 the row starts at x0 - CE, otherwise
+  // at x0, and it has TA / CE + 1 chunks. Items are numbered velocity-major
+  // and dealt to the threads in turn; each thread keeps its items' element
+  // offsets (plane term excluded, z neighbour included) and stage offsets.
+  constexpr int NCH0 = TA / CE;
+  constexpr int NFI = coop_items<LF, PAR, TB, NCH0>();
+  constexpr int KF = COOP ? (NFI + NT - 1) / NT : 1;
+  unsigned fsrc[KF], fdst[KF];
+  unsigned fmz = 0u, fpz = 0u;   // items reading plane c - 1 / c + 1
+  if constexpr (COOP) {
+#pragma unroll
+    for (int k = 0; k < KF; ++k) {
+      fsrc[k] = 0u;
+      fdst[k] = 0u;
+      const int i = tid + k * NT;
+      int base = 0;
+      static_for<0, QF>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        constexpr int nch = NCH0 + ((PAR == 1 && LF::ex(q) != 0) ? 1 : 0);
+        if (i >= base && i < base + TB * nch) {
+          const int r = (i - base) / nch, j = (i - base) % nch;
+          constexpr int slot = PAR == 0 ? q : LF::opp(q);
+          constexpr int dx = PAR == 0 ? 0 : -LF::ex(q), dy = PAR == 0 ? 0 : -LF::ey(q);
+          constexpr int dz = PAR == 0 ? 0 : -LF::ez(q);
+          const int x = wrap_mod(a0 + CE * j - (dx < 0 ? CE : 0), NA);
+          const int y = wrap_mod(b0 + r + dy, NB);
+          fsrc[k] = pop_ix<LF>(slot, (unsigned)(x + NA * y)) + (unsigned)(dz * (int)fplane);
+          fdst[k] = (unsigned)(((q * TB + r) * FROW + CE * j) * (int)sizeof(T));
+          if (dz < 0) fmz |= 1u << k;
+          if (dz > 0) fpz |= 1u << k;
+        }
+        base += TB * nch;
+      });
+    }
+  }
+
   auto issue = [&](int cg, int cf, int s, unsigned& gm, unsigned& fm) {
     gm = 0u;
     fm = 0u;
@@ -661,7 +724,24 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
         });
       }
     });
-    if (active) {
+    if constexpr (COOP) {
+      // The block's f chunks of plane cf (this thread's share, fixed per
+      // thread; items that read plane cf -+ 1 wrap at the domain's z ends).
+      const unsigned sf = s_stage_u32 + (unsigned)(s * (FST + GST)) * 4u;
+      const unsigned cbase = (unsigned)cf * fplane;
+      const bool zwrap = (cf == 0) || (cf == NC - 1);
+      static_for<0, KF>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        if ((k + 1) * NT <= NFI || tid + k * NT < NFI) {
+          unsigned e = fsrc[k] + cbase;
+          if (zwrap) {
+            if (cf == 0 && ((fmz >> k) & 1u)) e += (unsigned)NC * fplane;
+            if (cf == NC - 1 && ((fpz >> k) & 1u)) e -= (unsigned)NC * fplane;
+          }
+          cp_async16(sf + fdst[k], fb + e);
+        }
+      });
+    } else if (active) {
       const unsigned sf = s_stage_u32 + (unsigned)(s * (FST + GST) + tid) * 4u;
       static_for<0, QF>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
@@ -723,12 +803,17 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
   // the plane being collided; rotated every plane, compile-time indices).
   unsigned gmq[NST], fmq[NST];
   int st = 0;   // stage holding plane c
+  // Planes in flight ahead of the current one: NST per-thread stages are
+  // refilled at the end of the plane that consumed them; COOP stages only
+  // after the next plane's first barrier, so one of the NST is always being
+  // drained.
+  constexpr int AHEAD = COOP ? NST - 1 : NST;
   if constexpr (STAGED) {
 #pragma unroll
     for (int k = 0; k < NST; ++k) {
       gmq[k] = fmq[k] = 0u;
-      if (c0 + k < c1) issue(c0 + k + H, c0 + k, k, gmq[k], fmq[k]);
-      cp_async_commit();
+      if (k < AHEAD && c0 + k < c1) issue(c0 + k + H, c0 + k, k, gmq[k], fmq[k]);
+      if (k < AHEAD) cp_async_commit();
     }
   }
   if constexpr (CH) {
@@ -739,7 +824,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
 
   for (int c = c0; c < c1; ++c) {
     const unsigned gms = gmq[0], fms = fmq[0];
-    if constexpr (STAGED) cp_async_wait<NST - 1>();   // plane c has landed; the later ones may be in flight
+    if constexpr (STAGED) cp_async_wait<AHEAD - 1>();   // plane c has landed; the later ones may be in flight
     if constexpr (CH) {
       if constexpr (STAGED) produce_staged(c + 2, st, gms, g2);
       else produce(c + 2, g2);
@@ -750,6 +835,15 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
       if constexpr (STAGED) produce_staged(c + 1, st, gms, g1);
       else produce(c + 1, g1);
       __syncthreads();
+    }
+    if constexpr (COOP) {
+      // Every thread is past plane c - 1: refill its stage with plane c + NST - 1.
+      const int sn = (st == 0) ? NST - 1 : st - 1;
+      unsigned gnext = 0u, fnext = 0u;
+      if (c + NST - 1 < c1) issue(c + NST - 1 + H, c + NST - 1, sn, gnext, fnext);
+      cp_async_commit();
+      gmq[NST - 1] = gnext;
+      fmq[NST - 1] = fnext;
     }
 
     if (active) {
@@ -793,7 +887,17 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
 
       // Pre-collision f (AA pattern).
       float f[QF];
-      if constexpr (STAGED) {
+      if constexpr (COOP) {
+        // Row (q, ty) of the stage; an odd step's x - e_q sits at tx - e_x
+        // from the row's x0 (+ CE where the row starts at x0 - CE).
+        const T* fs = reinterpret_cast<const T*>(stage_f(st)) + ty * FROW + tx;
+        static_for<0, QF>([&](auto qc) {
+          constexpr int q = decltype(qc)::value;
+          constexpr int ex = LF::ex(q);
+          constexpr int off = PAR == 0 ? 0 : (ex > 0 ? CE - 1 : (ex < 0 ? 1 : 0));
+          f[q] = Codec<T>::dec(fs[q * TB * FROW + off], pow2_scale<LF>(q), 0.0f);
+        });
+      } else if constexpr (STAGED) {
         const float* fs = stage_f(st);
 #pragma unroll
         for (int q = 0; q < QF; ++q) f[q] = staged(fs[q * NT + tid], fms, q, q, false);
@@ -890,8 +994,13 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
     // the fewest values are live), and rotate the half-select bits.
     if constexpr (STAGED) {
       unsigned gnext = 0u, fnext = 0u;
-      if (c + NST < c1) issue(c + NST + H, c + NST, st, gnext, fnext);
-      cp_async_commit();
+      if constexpr (!COOP) {
+        if (c + NST < c1) issue(c + NST + H, c + NST, st, gnext, fnext);
+        cp_async_commit();
+      } else {
+        gnext = gmq[NST - 1];
+        fnext = fmq[NST - 1];
+      }
 #pragma unroll
       for (int k = 0; k + 1 < NST; ++k) {
         gmq[k] = gmq[k + 1];
@@ -930,7 +1039,7 @@ template <int FAM, int DIM, typename T, int PAR, int ROW>
 __global__ void __launch_bounds__(Geom<FAM, DIM, T>::TA * Geom<FAM, DIM, T>::TB, Geom<FAM, DIM, T>::MINB)
 step_kernel(const StepArgs args) {
   constexpr int TA = Geom<FAM, DIM, T>::TA, TB = Geom<FAM, DIM, T>::TB;
-  using SM = TileSmem<FAM, DIM, T, TA, TB>;
+  using SM = TileSmem<FAM, DIM, T, TA, TB, (DIM == 3) && (ROW == 1) && (PAR >= 0)>;
   extern __shared__ __align__(16) float dyn_smem[];
   float* s_stage = dyn_smem;
   float* s_phi = dyn_smem + SM::STAGE;
@@ -955,7 +1064,7 @@ step_kernel(const StepArgs args) {
 template <int FAM, int DIM, typename T, int PAR, int ROW>
 void launch_step_par(const StepArgs& args, cudaStream_t stream) {
   constexpr int TA = Geom<FAM, DIM, T>::TA, TB = Geom<FAM, DIM, T>::TB;
-  constexpr size_t smem = TileSmem<FAM, DIM, T, TA, TB>::BYTES;
+  constexpr size_t smem = TileSmem<FAM, DIM, T, TA, TB, (DIM == 3) && (ROW == 1) && (PAR >= 0)>::BYTES;
   static const cudaError_t attr = cudaFuncSetAttribute(
       step_kernel<FAM, DIM, T, PAR, ROW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   (void)attr;
