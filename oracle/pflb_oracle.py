@@ -7,9 +7,11 @@ Layout used throughout:
     lattice tables below.
 
 Lattices (Sec. III and Sec. IV): D2Q9 for both population sets in 2D; D3Q19
-for the hydrodynamic set and D3Q7 for the phase-field set in 3D, c_s^2 = 1/3
-for all of them (Sec. IV). The stencils of Sec. III use the hydrodynamic
-lattice's weights (Reading R7).
+(or D3Q27, the paper's own 3D hydrodynamic lattice, Sec. IV) for the
+hydrodynamic set and D3Q7 for the phase-field set in 3D, c_s^2 = 1/3 for all
+of them (Sec. IV). The 3D stencils of Sec. III use the D3Q19 weights
+(Readings R7, R20). The hydrodynamic collision is BGK or, on D3Q27, the
+multiple-relaxation-time operator of Sec. IV (Reading R20).
 
 Streaming is the plain two-array "push" form: every post-collision population
 moves to x + e in a fresh array. Walls (when enabled) are the planes
@@ -29,7 +31,8 @@ import numpy as np
 
 __all__ = [
     "FAKHARI2017", "CHAI2018", "HU2019", "LIANG2014", "LIANG2018", "FAMILY_NAMES",
-    "Lattice", "D2Q9", "D3Q19", "D3Q7", "lattices_for",
+    "Lattice", "D2Q9", "D3Q19", "D3Q27", "D3Q7", "lattices_for", "lattices_of",
+    "mrt_moment_matrix", "mrt_collide",
     "default_params", "derived", "State",
     "gradient", "laplacian", "lagrange_gamma", "nonlocal_R",
     "density", "kinematic_viscosity",
@@ -86,18 +89,36 @@ _EDGES = [(1, 1, 0), (-1, -1, 0), (1, -1, 0), (-1, 1, 0),
 D3Q19 = Lattice("D3Q19", [(0, 0, 0)] + _FACES + _EDGES,
                 [1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
 
+# D3Q27 hydrodynamic lattice (Sec. IV: the paper's NS lattice in 3D): rest
+# 8/27, faces 2/27, edges 1/54, corners 1/216; velocity order: D3Q19's, then
+# the eight corners as opposite pairs.
+_CORNERS = [(1, 1, 1), (-1, -1, -1), (1, 1, -1), (-1, -1, 1),
+            (1, -1, 1), (-1, 1, -1), (-1, 1, 1), (1, -1, -1)]
+D3Q27 = Lattice("D3Q27", [(0, 0, 0)] + _FACES + _EDGES + _CORNERS,
+                [8 / 27] + [2 / 27] * 6 + [1 / 54] * 12 + [1 / 216] * 8)
+
 # D3Q7 phase-field lattice with c_s^2 = 1/3 (Sec. IV): the second-moment
 # condition 2 w_1 = c_s^2 fixes w_1 = 1/6 and leaves w_0 = 0.
 D3Q7 = Lattice("D3Q7", [(0, 0, 0)] + _FACES, [0.0] + [1 / 6] * 6)
 
 
-def lattices_for(dim):
-    """(phase-field lattice, hydrodynamic lattice, stencil lattice)."""
+def lattices_for(dim, lattice_f=19):
+    """(phase-field lattice, hydrodynamic lattice, stencil lattice). In 3D the
+    hydrodynamic lattice is D3Q19 or D3Q27; the stencils keep the D3Q19
+    weights either way (Reading R20)."""
     if dim == 2:
         return D2Q9, D2Q9, D2Q9
     if dim == 3:
-        return D3Q7, D3Q19, D3Q19
+        if lattice_f == 19:
+            return D3Q7, D3Q19, D3Q19
+        if lattice_f == 27:
+            return D3Q7, D3Q27, D3Q19
+        raise ValueError("lattice_f must be 19 or 27")
     raise ValueError("dim must be 2 or 3")
+
+
+def lattices_of(P):
+    return lattices_for(P["dim"], P.get("lattice_f", 19))
 
 
 # --------------------------------------------------------------------------
@@ -115,7 +136,10 @@ def default_params(**kw):
              eta_ch=1.0,             # Reading R12
              gravity=(0.0, 0.0, 0.0), force_density=(0.0, 0.0, 0.0),
              lundgren_A=0.0, wall_u=(0.0, 0.0), grad_eps=1e-4,
-             freeze_phi=0)
+             freeze_phi=0,
+             lattice_f=19,           # 3D hydrodynamic lattice: 19 or 27
+             collision=0,            # 0 BGK, 1 MRT (D3Q27, Reading R20)
+             mrt_s_bulk=1.0, mrt_s_ho=1.0)
     p.update(kw)
     return p
 
@@ -379,6 +403,47 @@ def force_liang2018(lat, u, grad_rho, F):
 
 
 # --------------------------------------------------------------------------
+# Multiple-relaxation-time collision on D3Q27 (Sec. IV, Reading R20)
+# --------------------------------------------------------------------------
+def mrt_moment_matrix(lat):
+    """Raw moments m_ijk = sum_a e_ax^i e_ay^j e_az^k f_a, i, j, k in {0, 1, 2}:
+    the 27 x 27 matrix M (rows in the order of ``MRT_ORDERS``) and, per row, the
+    moment's (i, j, k)."""
+    ijk = [(i, j, k) for k in range(3) for j in range(3) for i in range(3)]
+    M = np.array([[lat.ef[a, 0] ** i * lat.ef[a, 1] ** j * lat.ef[a, 2] ** k for a in range(lat.Q)]
+                  for (i, j, k) in ijk])
+    return M, ijk
+
+
+def mrt_collide(P, lat, f, feq, Fb, tau):
+    """f* = f - M^-1 S M (f - f_eq) + M^-1 (I - S/2) M F_b with the raw moments
+    of ``mrt_moment_matrix``. S relaxes (Reading R20): the traceless part of the
+    second-order moments (shear, the viscosity of Eq. fakhari_tau_model) and
+    the conserved and first-order moments at 1/tau; the trace
+    m_200 + m_020 + m_002 at mrt_s_bulk; every moment of order >= 3 at
+    mrt_s_ho. With both rates equal to 1/tau this is the BGK update."""
+    M, ijk = mrt_moment_matrix(lat)
+    Minv = np.linalg.inv(M)
+    shape = f.shape[1:]
+    w = 1.0 / tau
+    neq = np.tensordot(M, f - feq, axes=([1], [0]))       # (27, ...)
+    mF = np.tensordot(M, Fb, axes=([1], [0]))
+    sb, sh = P["mrt_s_bulk"], P["mrt_s_ho"]
+    rate = np.empty((27,) + shape)
+    order = [i + j + k for (i, j, k) in ijk]
+    for r, o in enumerate(order):
+        rate[r] = w if o <= 2 else sh
+    # second order: S acts on (m_200, m_020, m_002) as w (I - J/3) + s_b J/3
+    diag = [ijk.index(t) for t in ((2, 0, 0), (0, 2, 0), (0, 0, 2))]
+    post = -rate * neq + (1.0 - 0.5 * rate) * mF
+    tr_neq = sum(neq[d] for d in diag) / 3.0
+    tr_F = sum(mF[d] for d in diag) / 3.0
+    for d in diag:
+        post[d] = -(w * (neq[d] - tr_neq) + sb * tr_neq) + (mF[d] - 0.5 * (w * (mF[d] - tr_F) + sb * tr_F))
+    return f + np.tensordot(Minv, post, axes=([1], [0]))
+
+
+# --------------------------------------------------------------------------
 # State
 # --------------------------------------------------------------------------
 class State:
@@ -414,7 +479,7 @@ def macroscopic(P, st, gamma=None):
     Returns a dict with phi, rho, nu, tau, tau_phi, grad_phi, lap_phi, mu, p,
     u, F (total force density) and the family-specific terms.
     """
-    lg, lf, ls = lattices_for(P["dim"])
+    lg, lf, ls = lattices_of(P)
     c = derived(P)
     walls = _walls(P)
     fam = P["family"]
@@ -524,7 +589,7 @@ def macroscopic(P, st, gamma=None):
 # --------------------------------------------------------------------------
 def collide(P, st, m):
     """Post-collision populations g*, f* and the phi*u of this step (Liang2014)."""
-    lg, lf, _ = lattices_for(P["dim"])
+    lg, lf, _ = lattices_of(P)
     fam = P["family"]
     phi, u, rho = m["phi"], m["u"], m["rho"]
     g, f = st.g, st.f
@@ -574,7 +639,10 @@ def collide(P, st, m):
         else:
             Fb = force_guo(lf, m["F"], rho, u)
     tau = m["tau"]
-    fs = f - (f - feq) / tau + (1.0 - 1.0 / (2.0 * tau)) * Fb          # Eq. (fakhari_f_simplified)
+    if P.get("collision", 0) == 1:
+        fs = mrt_collide(P, lf, f, feq, Fb, tau)                        # Sec. IV, Reading R20
+    else:
+        fs = f - (f - feq) / tau + (1.0 - 1.0 / (2.0 * tau)) * Fb      # Eq. (fakhari_f_simplified)
     return gs, fs, phiu_new
 
 
@@ -620,7 +688,7 @@ def init_state(P, phi0, u0, dtype=np.float64):
     """Populations at equilibrium with the given phi and u and p = 0 (Reading R8).
     Every later step works in the dtype of the state (float64 unless asked
     otherwise; float32 only serves to size the effect of FP32 rounding)."""
-    lg, lf, ls = lattices_for(P["dim"])
+    lg, lf, ls = lattices_of(P)
     phi0 = np.asarray(phi0, dtype=dtype)
     u0 = np.asarray(u0, dtype=dtype)
     assert phi0.shape == _shape(P) and u0.shape == (P["dim"],) + _shape(P)
@@ -649,7 +717,7 @@ def init_state(P, phi0, u0, dtype=np.float64):
 
 def step(P, st, gamma=None):
     """One coupled time step: macroscopic stage, collision of both sets, streaming."""
-    lg, lf, _ = lattices_for(P["dim"])
+    lg, lf, _ = lattices_of(P)
     m = macroscopic(P, st, gamma)
     gs, fs, phiu_new = collide(P, st, m)
     if P["freeze_phi"]:
@@ -720,7 +788,7 @@ def step_at_cells(P, st, cells, gamma=None):
     Pp["ny"] = n
     if d == 3:
         Pp["nz"] = n
-    lg, lf, _ = lattices_for(d)
+    lg, lf, _ = lattices_of(P)
     g_out = np.zeros((lg.Q, len(cells)))
     f_out = np.zeros((lf.Q, len(cells)))
     for i, cell in enumerate(cells):
@@ -751,7 +819,7 @@ def pack_state(P, st):
 
 
 def unpack_state(P, blob, t=0):
-    lg, lf, _ = lattices_for(P["dim"])
+    lg, lf, _ = lattices_of(P)
     shape = _shape(P)
     blob = np.asarray(blob, dtype=np.float64).reshape(-1, int(np.prod(shape)))
     g = blob[: lg.Q].reshape((lg.Q,) + shape).copy()

@@ -21,7 +21,7 @@ RNG = np.random.default_rng(7)
 
 
 # ------------------------------------------------------------------ lattices
-@pytest.mark.parametrize("lat", [O.D2Q9, O.D3Q19, O.D3Q7], ids=lambda l: l.name)
+@pytest.mark.parametrize("lat", [O.D2Q9, O.D3Q19, O.D3Q27, O.D3Q7], ids=lambda l: l.name)
 def test_lattice_low_moments(lat):
     cs2 = 1.0 / 3.0
     assert np.isclose(lat.w.sum(), 1.0, atol=1e-15)
@@ -35,7 +35,7 @@ def test_lattice_low_moments(lat):
         assert lat.w[lat.opp[a]] == lat.w[a]
 
 
-@pytest.mark.parametrize("lat", [O.D2Q9, O.D3Q19], ids=lambda l: l.name)
+@pytest.mark.parametrize("lat", [O.D2Q9, O.D3Q19, O.D3Q27], ids=lambda l: l.name)
 def test_lattice_fourth_moment_isotropic(lat):
     """sum w e_i e_j e_k e_l = c_s^4 (d_ij d_kl + d_ik d_jl + d_il d_jk): the
     condition for the (e.u)^2/(2 c_s^4) equilibrium terms to give u u."""
@@ -298,8 +298,7 @@ def test_init_is_equilibrium(fam):
 def _reflect_x(P, st):
     """Mirror a state about x: field index x -> nx-1-x, populations a -> a' with
     e_x negated."""
-    d = P["dim"]
-    lg, lf, _ = O.lattices_for(d)
+    lg, lf, _ = O.lattices_of(P)
 
     def refl(lat, pop):
         out = np.empty_like(pop)
