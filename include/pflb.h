@@ -103,6 +103,16 @@ typedef struct pflb_params {
   double grad_eps;      /* regularisation of the interface normal,
                            n = grad phi / sqrt(|grad phi|^2 + grad_eps^2)
                            (1e-4; the paper leaves n undefined at 0) */
+  int32_t lattice_f;    /* 3D hydrodynamic lattice: 19 (D3Q19; 0 means 19) or 27
+                           (D3Q27, the paper's 3D lattice, Sec. IV); 2D: 0 or 9 */
+  int32_t collision;    /* 0 BGK (Sec. II B); 1 multiple-relaxation-time (Sec. IV,
+                           D3Q27 only): raw moments sum f e_x^i e_y^j e_z^k,
+                           i,j,k <= 2; conserved, first-order and traceless
+                           second-order moments at 1/tau, the trace of the
+                           second-order moments at mrt_s_bulk, orders >= 3 at
+                           mrt_s_ho; forcing (I - S/2) in moment space */
+  double mrt_s_bulk;    /* MRT rate of the second-moment trace, in (0, 2) */
+  double mrt_s_ho;      /* MRT rate of the moments of order >= 3, in (0, 2) */
 } pflb_params;
 
 /* Bookkeeping of one state: sums over all cells of its macroscopic fields. */
@@ -164,8 +174,8 @@ int pflb_get_fields(pflb_handle* h, float* phi, float* u, float* p);
 
 /* Size in floats of the canonical state: Qg*N populations g, Qf*N
  * populations f (both post-streaming, i.e. what the next step reads, in the
- * velocity order of pflb_lattice), then for Cahn-Hilliard d*N values of
- * phi*u of the previous step. */
+ * velocity order of pflb_lattice; Qf = 27 with lattice_f = 27), then for
+ * Liang2014 and Liang2018 d*N values of phi*u of the previous step. */
 int64_t pflb_state_floats(const pflb_handle* h);
 
 /* Write / read the canonical FP32 state (host or device buffer of
@@ -187,7 +197,8 @@ double pflb_bytes_per_update(const pflb_handle* h);
 int pflb_set_chunk(pflb_handle* h, int32_t chunk);
 
 /* Velocity set of a lattice in canonical order. which: 0 = phase field (g),
- * 1 = hydrodynamics (f). q receives Q; e receives 3*Q ints (ex, ey, ez per
+ * 1 = hydrodynamics (f: D2Q9 / D3Q19), 2 = the D3Q27 hydrodynamic lattice
+ * (dim 3 only). q receives Q; e receives 3*Q ints (ex, ey, ez per
  * velocity, ez = 0 in 2D) and w receives Q weights; either may be NULL. */
 int pflb_lattice(int32_t dim, int32_t which, int32_t* q, int32_t* e, double* w);
 

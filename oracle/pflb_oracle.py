@@ -102,14 +102,14 @@ D3Q27 = Lattice("D3Q27", [(0, 0, 0)] + _FACES + _EDGES + _CORNERS,
 D3Q7 = Lattice("D3Q7", [(0, 0, 0)] + _FACES, [0.0] + [1 / 6] * 6)
 
 
-def lattices_for(dim, lattice_f=19):
+def lattices_for(dim, lattice_f=0):
     """(phase-field lattice, hydrodynamic lattice, stencil lattice). In 3D the
     hydrodynamic lattice is D3Q19 or D3Q27; the stencils keep the D3Q19
     weights either way (Reading R20)."""
     if dim == 2:
         return D2Q9, D2Q9, D2Q9
     if dim == 3:
-        if lattice_f == 19:
+        if lattice_f in (0, 19):
             return D3Q7, D3Q19, D3Q19
         if lattice_f == 27:
             return D3Q7, D3Q27, D3Q19
@@ -118,7 +118,7 @@ def lattices_for(dim, lattice_f=19):
 
 
 def lattices_of(P):
-    return lattices_for(P["dim"], P.get("lattice_f", 19))
+    return lattices_for(P["dim"], P.get("lattice_f", 0))
 
 
 # --------------------------------------------------------------------------
@@ -137,7 +137,7 @@ def default_params(**kw):
              gravity=(0.0, 0.0, 0.0), force_density=(0.0, 0.0, 0.0),
              lundgren_A=0.0, wall_u=(0.0, 0.0), grad_eps=1e-4,
              freeze_phi=0,
-             lattice_f=19,           # 3D hydrodynamic lattice: 19 or 27
+             lattice_f=0,            # 3D hydrodynamic lattice: 19 (or 0) or 27
              collision=0,            # 0 BGK, 1 MRT (D3Q27, Reading R20)
              mrt_s_bulk=1.0, mrt_s_ho=1.0)
     p.update(kw)

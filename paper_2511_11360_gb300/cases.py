@@ -30,7 +30,7 @@ def params(**kw):
              visc_interp=0, sigma=1e-3, W=4.0, M=0.1, lambda_hybrid=0.9,
              eta_ch=1.0, gravity=(0.0, 0.0, 0.0), force_density=(0.0, 0.0, 0.0),
              lundgren_A=0.0, wall_u=(0.0, 0.0), grad_eps=1e-4, freeze_phi=0,
-             lattice_f=19, collision=0, mrt_s_bulk=1.0, mrt_s_ho=1.0)
+             lattice_f=0, collision=0, mrt_s_bulk=1.0, mrt_s_ho=1.0)
     p.update(kw)
     return p
 

@@ -45,6 +45,8 @@ extern "C" int pflb_adjoint(pflb_handle* h, int64_t nsteps, int32_t checkpoint_e
   const pflb_params& p = h->prm;
   if (h->family != PFLB_CAC_FAKHARI2017)
     return handle_fail(h, PFLB_EINVAL, "pflb_adjoint covers the Fakhari2017 family");
+  if (h->QF != (h->dim == 2 ? 9 : 19))
+    return handle_fail(h, PFLB_EINVAL, "pflb_adjoint covers the D2Q9 and D3Q19 hydrodynamic lattices (BGK)");
   if (p.bc_y != 0) return handle_fail(h, PFLB_EINVAL, "pflb_adjoint covers periodic domains");
   if (h->storage != PFLB_FP32) return handle_fail(h, PFLB_EINVAL, "pflb_adjoint needs FP32 storage");
   if (p.rho_H != p.rho_L) return handle_fail(h, PFLB_EINVAL, "pflb_adjoint covers density ratio 1");

@@ -88,6 +88,15 @@ int validate(const pflb_params* p, char* msg, size_t n) {
   if (!(eta > 0.0)) return snprintf(msg, n, "eta must be > 0"), PFLB_EINVAL;
   if (!(3.0 * p->M / eta + 0.5 > 0.5)) return snprintf(msg, n, "tau_phi must exceed 1/2 (M > 0)"), PFLB_EINVAL;
   if (!(p->lundgren_A < 2.0)) return snprintf(msg, n, "lundgren_A must be < 2"), PFLB_EINVAL;
+  const int lf = p->lattice_f;
+  if (p->dim == 2 ? !(lf == 0 || lf == 9) : !(lf == 0 || lf == 19 || lf == 27))
+    return snprintf(msg, n, "lattice_f must be 9 in 2D and 19 or 27 in 3D (0: default)"), PFLB_EINVAL;
+  if (p->collision != 0 && p->collision != 1) return snprintf(msg, n, "collision must be 0 (BGK) or 1 (MRT)"), PFLB_EINVAL;
+  if (p->collision == 1) {
+    if (lf != 27) return snprintf(msg, n, "the MRT collision is defined on D3Q27 (lattice_f = 27)"), PFLB_EINVAL;
+    if (!(p->mrt_s_bulk > 0.0 && p->mrt_s_bulk < 2.0 && p->mrt_s_ho > 0.0 && p->mrt_s_ho < 2.0))
+      return snprintf(msg, n, "MRT rates must lie in (0, 2)"), PFLB_EINVAL;
+  }
   return PFLB_OK;
 }
 
@@ -137,6 +146,10 @@ DevParams derive(const pflb_params* p) {
   d.wall_u[1] = (float)p->wall_u[1];
   d.eps2 = (float)(p->grad_eps * p->grad_eps);
   d.gref = (float)(0.5 * (p->phi_H + p->phi_L));
+  d.lat = (p->dim == 3 && p->lattice_f == 27) ? 1 : 0;
+  d.mrt = p->collision == 1 ? 1 : 0;
+  d.mrt_sb = (float)p->mrt_s_bulk;
+  d.mrt_sh = (float)p->mrt_s_ho;
   return d;
 }
 
@@ -289,7 +302,7 @@ int pflb_create(const pflb_params* params, void* cuda_stream, pflb_handle** out)
   h->stream = static_cast<cudaStream_t>(cuda_stream);
   h->dim = params->dim;
   h->QG = params->dim == 2 ? 9 : 7;
-  h->QF = params->dim == 2 ? 9 : 19;
+  h->QF = params->dim == 2 ? 9 : (params->lattice_f == 27 ? 27 : 19);
   h->storage = params->storage;
   h->family = params->family;
   h->N = (long long)params->nx * params->ny * params->nz;
@@ -513,7 +526,7 @@ int pflb_set_chunk(pflb_handle* h, int32_t chunk) {
 }
 
 int pflb_lattice(int32_t dim, int32_t which, int32_t* q, int32_t* e, double* w) {
-  if ((dim != 2 && dim != 3) || (which != 0 && which != 1)) return PFLB_EINVAL;
+  if ((dim != 2 && dim != 3) || which < 0 || which > 2 || (which == 2 && dim != 3)) return PFLB_EINVAL;
   auto put = [&](auto L) {
     using Lt = decltype(L);
     if (q) *q = Lt::Q;
@@ -523,14 +536,13 @@ int pflb_lattice(int32_t dim, int32_t which, int32_t* q, int32_t* e, double* w) 
         e[3 * a + 1] = Lt::ey(a);
         e[3 * a + 2] = Lt::ez(a);
       }
-      if (w) w[a] = Lt::Q == 9 ? (a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0))
-                  : Lt::Q == 7 ? (a == 0 ? 0.0 : 1.0 / 6.0)
-                  : (a == 0 ? 1.0 / 3.0 : (a < 7 ? 1.0 / 18.0 : 1.0 / 36.0));
+      if (w) w[a] = Lt::wx(a);
     }
   };
   if (dim == 2) put(D2Q9{});
   else if (which == 0) put(D3Q7{});
-  else put(D3Q19{});
+  else if (which == 1) put(D3Q19{});
+  else put(D3Q27{});
   return PFLB_OK;
 }
 

@@ -14,8 +14,11 @@ namespace pflb {
 struct TileShape {
   int ta, tb, minb;
 };
-__host__ __device__ constexpr TileShape tile_shape(int family, int dim, int storage) {
-  return (void)storage, dim == 2 ? TileShape{128, 1, 4} : family == 3 ? TileShape{32, 6, 2} : TileShape{32, 4, 3};
+__host__ __device__ constexpr TileShape tile_shape(int family, int dim, int storage, int lat = 0) {
+  // D3Q27 holds 27 populations (and with MRT their moments) a thread: two blocks per SM.
+  return (void)storage, dim == 2 ? TileShape{128, 1, 4}
+                       : family == 3 ? TileShape{32, 6, 2}
+                       : lat == 1 ? TileShape{32, 4, 2} : TileShape{32, 4, 3};
 }
 
 struct StepArgs {

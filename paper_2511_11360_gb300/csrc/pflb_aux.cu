@@ -84,10 +84,10 @@ void gamma_sums(int dim, int storage, const GammaArgs& a, cudaStream_t s) {
 // Canonical state <-> storage. The canonical f_q(x) is what the next step
 // reads: slot q of x before an even step; before an odd step slot opp(q) of
 // x - e_q, or slot q of x itself where x - e_q lies beyond a wall.
-template <int DIM, typename T>
+template <int DIM, typename T, int LAT>
 __global__ void canon_kernel(const CanonArgs a) {
-  using LG = typename Lattices<DIM>::G;
-  using LF = typename Lattices<DIM>::F;
+  using LG = typename Lattices<DIM, LAT>::G;
+  using LF = typename Lattices<DIM, LAT>::F;
   constexpr int QG = LG::Q, QF = LF::Q;
   const DevParams& P = a.p;
   const long long N = a.N;
@@ -149,7 +149,9 @@ template <int DIM, typename T>
 static void launch_canon(const CanonArgs& a, cudaStream_t s) {
   long long want = (a.N + 255) / 256;
   long long cap = 16LL * sm_count();
-  canon_kernel<DIM, T><<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(a);
+  const unsigned grid = (unsigned)(want < cap ? want : cap);
+  if (DIM == 3 && a.p.lat == 1) canon_kernel<DIM, T, (DIM == 3 ? 1 : 0)><<<grid, 256, 0, s>>>(a);
+  else canon_kernel<DIM, T, 0><<<grid, 256, 0, s>>>(a);
 }
 
 void canon_copy(int dim, int storage, const CanonArgs& a, cudaStream_t s) {

@@ -99,6 +99,33 @@ struct D3Q19 {
   }
 };
 
+// D3Q27 (Sec. IV: the paper's 3D hydrodynamic lattice): D3Q19's nineteen,
+// then the corners (1,1,1) (-1,-1,-1) (1,1,-1) (-1,-1,1) (1,-1,1) (-1,1,-1)
+// (-1,1,1) (1,-1,-1); weights 8/27, 2/27, 1/54, 1/216.
+struct D3Q27 {
+  static constexpr int Q = 27;
+  __host__ __device__ static constexpr int ex(int a) {
+    constexpr int t[27] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, -1, 1};
+    return t[a];
+  }
+  __host__ __device__ static constexpr int ey(int a) {
+    constexpr int t[27] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, -1, 1, 1, -1};
+    return t[a];
+  }
+  __host__ __device__ static constexpr int ez(int a) {
+    constexpr int t[27] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1, 1, -1, -1, 1, 1, -1, 1, -1};
+    return t[a];
+  }
+  __host__ __device__ static constexpr double wx(int a) {
+    return a == 0 ? 8.0 / 27.0 : (a < 7 ? 2.0 / 27.0 : (a < 19 ? 1.0 / 54.0 : 1.0 / 216.0));
+  }
+  __host__ __device__ static constexpr float w(int a) { return (float)wx(a); }
+  __host__ __device__ static constexpr float wlo(int a) { return (float)(wx(a) - (double)w(a)); }
+  __host__ __device__ static constexpr int opp(int a) {
+    return a == 0 ? 0 : ((a % 2 == 1) ? a + 1 : a - 1);
+  }
+};
+
 // w_a * x with the weight carried as hi + lo (w = w_hi + w_lo to ~1e-16):
 // the FP32 weights alone have sum_a w_a e_a e_a = (1 + 7.45e-9) I / 3 on D2Q9
 // and D3Q19, which biases every equilibrium moment and made the momentum grow
@@ -121,9 +148,12 @@ __host__ __device__ __forceinline__ unsigned pop_ix(int q, unsigned cell) {
 }
 
 // Lattice triple per dimension: phase field g, hydrodynamics f, stencil.
-template <int DIM> struct Lattices;
-template <> struct Lattices<2> { using G = D2Q9; using F = D2Q9; using S = D2Q9; };
-template <> struct Lattices<3> { using G = D3Q7; using F = D3Q19; using S = D3Q19; };
+// LAT = 1 selects the D3Q27 hydrodynamic lattice in 3D; the stencils keep
+// the D3Q19 weights.
+template <int DIM, int LAT = 0> struct Lattices;
+template <> struct Lattices<2, 0> { using G = D2Q9; using F = D2Q9; using S = D2Q9; };
+template <> struct Lattices<3, 0> { using G = D3Q7; using F = D3Q19; using S = D3Q19; };
+template <> struct Lattices<3, 1> { using G = D3Q7; using F = D3Q27; using S = D3Q19; };
 
 // ---------------------------------------------------------------------------
 // Parameters in the form the kernels use (host-derived, FP32).
@@ -149,6 +179,9 @@ struct DevParams {
   float wall_u[2];          // bottom, top
   float eps2;               // grad_eps^2 (normal regularisation)
   float gref;               // rest-state offset of g in 16-bit storage
+  int32_t lat;              // 3D hydrodynamic lattice: 0 D3Q19, 1 D3Q27
+  int32_t mrt;              // 1: multiple-relaxation-time collision (D3Q27)
+  float mrt_sb, mrt_sh;     // MRT rates: trace of the second moments, orders >= 3
 };
 
 // Observables accumulated by one pass (one slot of the per-step ring).

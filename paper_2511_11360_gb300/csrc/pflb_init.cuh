@@ -8,11 +8,11 @@ namespace pflb {
 // One thread per cell (grid-stride). g goes to the source array in the
 // canonical slot order; f goes to the AA array in the even-step layout
 // (slot q of the cell holds f_q); Liang2014 and Liang2018 also store phi*u.
-template <int FAM, int DIM, typename T>
+template <int FAM, int DIM, typename T, int LAT = 0>
 __global__ void init_kernel(const InitArgs args) {
-  using LG = typename Lattices<DIM>::G;
-  using LF = typename Lattices<DIM>::F;
-  using LS = typename Lattices<DIM>::S;
+  using LG = typename Lattices<DIM, LAT>::G;
+  using LF = typename Lattices<DIM, LAT>::F;
+  using LS = typename Lattices<DIM, LAT>::S;
   constexpr int QG = LG::Q, QF = LF::Q, QS = LS::Q;
   const DevParams& P = args.p;
   const long long N = args.N;
@@ -82,10 +82,10 @@ __global__ void init_kernel(const InitArgs args) {
   }
 }
 
-template <int FAM, int DIM, typename T>
+template <int FAM, int DIM, typename T, int LAT = 0>
 void launch_init(const InitArgs& a, cudaStream_t s) {
   const long long blocks = (a.N + 255) / 256;
-  init_kernel<FAM, DIM, T><<<(unsigned)(blocks < 65535 * 16 ? blocks : 65535 * 16), 256, 0, s>>>(a);
+  init_kernel<FAM, DIM, T, LAT><<<(unsigned)(blocks < 65535 * 16 ? blocks : 65535 * 16), 256, 0, s>>>(a);
 }
 
 // Per-family dispatch over dimension and storage (instantiated once per
@@ -96,10 +96,14 @@ void step_dispatch(int dim, int storage, const StepArgs& a, cudaStream_t s) {
     if (storage == 0) launch_step<FAM, 2, float>(a, s);
     else if (storage == 1) launch_step<FAM, 2, __half>(a, s);
     else launch_step<FAM, 2, __nv_bfloat16>(a, s);
-  } else {
+  } else if (a.p.lat == 0) {
     if (storage == 0) launch_step<FAM, 3, float>(a, s);
     else if (storage == 1) launch_step<FAM, 3, __half>(a, s);
     else launch_step<FAM, 3, __nv_bfloat16>(a, s);
+  } else {
+    if (storage == 0) launch_step<FAM, 3, float, 1>(a, s);
+    else if (storage == 1) launch_step<FAM, 3, __half, 1>(a, s);
+    else launch_step<FAM, 3, __nv_bfloat16, 1>(a, s);
   }
 }
 
@@ -109,10 +113,14 @@ void init_dispatch(int dim, int storage, const InitArgs& a, cudaStream_t s) {
     if (storage == 0) launch_init<FAM, 2, float>(a, s);
     else if (storage == 1) launch_init<FAM, 2, __half>(a, s);
     else launch_init<FAM, 2, __nv_bfloat16>(a, s);
-  } else {
+  } else if (a.p.lat == 0) {
     if (storage == 0) launch_init<FAM, 3, float>(a, s);
     else if (storage == 1) launch_init<FAM, 3, __half>(a, s);
     else launch_init<FAM, 3, __nv_bfloat16>(a, s);
+  } else {
+    if (storage == 0) launch_init<FAM, 3, float, 1>(a, s);
+    else if (storage == 1) launch_init<FAM, 3, __half, 1>(a, s);
+    else launch_init<FAM, 3, __nv_bfloat16, 1>(a, s);
   }
 }
 

@@ -18,16 +18,17 @@
 #include <type_traits>
 
 #include "pflb_args.h"
+#include "pflb_mrt.cuh"
 #include "pflb_symsum.cuh"
 
 namespace pflb {
 
-template <int FAM, int DIM, typename T>
+template <int FAM, int DIM, typename T, int LAT = 0>
 struct Geom {
   static constexpr int STORAGE = std::is_same<T, float>::value ? 0 : 1;
-  static constexpr int TA = tile_shape(FAM, DIM, STORAGE).ta;
-  static constexpr int TB = tile_shape(FAM, DIM, STORAGE).tb;
-  static constexpr int MINB = tile_shape(FAM, DIM, STORAGE).minb;
+  static constexpr int TA = tile_shape(FAM, DIM, STORAGE, LAT).ta;
+  static constexpr int TB = tile_shape(FAM, DIM, STORAGE, LAT).tb;
+  static constexpr int MINB = tile_shape(FAM, DIM, STORAGE, LAT).minb;
 };
 
 
@@ -91,11 +92,13 @@ __device__ __forceinline__ float phi_star(const V& g) {
 // lap phi (and for Cahn-Hilliard mu, lap mu, phi*u of the previous step).
 // Outputs: post-collision g*, f*, u, p, rho.
 // ---------------------------------------------------------------------------
-template <int FAM, int DIM>
+template <int FAM, int DIM, int LAT = 0>
 struct Cell {
-  using LG = typename Lattices<DIM>::G;
-  using LF = typename Lattices<DIM>::F;
+  using LG = typename Lattices<DIM, LAT>::G;
+  using LF = typename Lattices<DIM, LAT>::F;
   static constexpr int QG = LG::Q, QF = LF::Q;
+  // Size of the MRT work array: 27 on D3Q27 (the collision has an MRT form), 1 otherwise.
+  static constexpr int MRT_Q = (QF == 27) ? 27 : 1;
 
   __device__ __forceinline__ static void collide(
       const DevParams& P, float (&g)[QG], float (&f)[QF], float phi, float phis,
@@ -282,7 +285,8 @@ struct Cell {
       // without a biased FP32 constant so the p -> f_eq -> p round trip is
       // unbiased.
       const float Xp = sum_nz + 0.5f * udg - wmul<LF>(0, rho * 1.5f * usq);
-      const float p3 = (DIM == 2) ? (Xp * 9.0f) / 5.0f : Xp * 1.5f;
+      // 1 - w_0 = 5/9 (D2Q9), 2/3 (D3Q19), 19/27 (D3Q27)
+      const float p3 = (LF::Q == 9) ? (Xp * 9.0f) / 5.0f : (LF::Q == 19 ? Xp * 1.5f : (Xp * 27.0f) / 19.0f);
       p = p3 / 3.0f;
       float uF = 0.0f, ua = 0.0f;
 #pragma unroll
@@ -290,6 +294,7 @@ struct Cell {
         uF += u[k] * F[k];
         ua += u[k] * cs2 * grho[k];
       }
+      float nq[MRT_Q];   // f - f_eq + F_b/2 (MRT, D3Q27)
 #pragma unroll
       for (int q = 0; q < QF; ++q) {
         float eu = 0.0f, eF = 0.0f, ea = 0.0f;
@@ -312,8 +317,11 @@ struct Cell {
           // u.grad rho terms cancel, leaving w (3 e.F + 3 (e.u)(e.grad rho)),
           // with ea = c_s^2 e.grad rho.
           Fq = wmul<LF>(q, 3.0f * eF + 9.0f * eu * ea);
+        if constexpr (MRT_Q == QF) nq[q] = (f[q] - feq) + 0.5f * Fq;
         f[q] = f[q] - (f[q] - feq) * itau + fw * Fq;
       }
+      if constexpr (MRT_Q == QF)
+        if (P.mrt) mrt_correct(f, nq, itau, P.mrt_sb, P.mrt_sh);
     } else {
       // f* = f - (f - f_eq) itau + fw F_b = f (1 - itau) + w (itau X + fw Y), with
       // f_eq = w X, X = sum f + 3 e.u + 4.5 (e.u)^2 - 1.5 u.u   Eq. (fakhari_feq),
@@ -334,6 +342,9 @@ struct Cell {
       const float omi = 1.0f - itau;
       const float itau3 = 3.0f * itau, fw3 = 3.0f * fw;
       const float ye0 = (FAM == FAM_FAKHARI) ? 0.0f : -3.0f * uFt;   // even part of Y at e = 0
+      // MRT (D3Q27): n = f - f_eq + F_b/2 = f - w (X - Y/2), collected before the update.
+      float nq[MRT_Q];
+      if constexpr (MRT_Q == QF) nq[0] = f[0] - wmul<LF>(0, s0 - 0.5f * ye0);
       f[0] = fmaf(f[0], omi, wmul<LF>(0, fmaf(itau, s0, fw * ye0)));
 #pragma unroll
       for (int q = 1; q < QF; ++q) {
@@ -351,9 +362,18 @@ struct Cell {
         if constexpr (FAM == FAM_FAKHARI) E = itau * fmaf(4.5f * eu, eu, s0);
         else E = fmaf(itau, fmaf(4.5f * eu, eu, s0), fw * fmaf(9.0f * eu, eF, ye0));
         const float O = fmaf(itau3, eu, fw3 * eF);
+        if constexpr (MRT_Q == QF) {
+          // X - Y/2 = (s0 + 4.5 (e.u)^2 - Y_even/2) +- (3 e.u - 1.5 e.F~)
+          const float xe = fmaf(4.5f * eu, eu, s0) - ((FAM == FAM_FAKHARI) ? 0.0f : 0.5f * fmaf(9.0f * eu, eF, ye0));
+          const float xo = fmaf(3.0f, eu, -1.5f * eF);
+          nq[q] = f[q] - wmul<LF>(q, xe + xo);
+          nq[qo] = f[qo] - wmul<LF>(qo, xe - xo);
+        }
         f[q] = fmaf(f[q], omi, wmul<LF>(q, E + O));
         f[qo] = fmaf(f[qo], omi, wmul<LF>(qo, E - O));
       }
+      if constexpr (MRT_Q == QF)
+        if (P.mrt) mrt_correct(f, nq, itau, P.mrt_sb, P.mrt_sh);
     }
   }
 };
@@ -370,7 +390,7 @@ __host__ __device__ constexpr int coop_items() {
 // ---------------------------------------------------------------------------
 // Shared-memory footprint of one tile march.
 // ---------------------------------------------------------------------------
-template <int FAM, int DIM, typename T, int TA, int TB, bool COOP = false>
+template <int FAM, int DIM, typename T, int TA, int TB, bool COOP = false, int LAT = 0>
 struct TileSmem {
   static constexpr bool CH = (FAM == FAM_LIANG);
   static constexpr int H = CH ? 2 : 1;
@@ -390,8 +410,9 @@ struct TileSmem {
   static constexpr bool STAGED = true;
   static constexpr int CE = 16 / (int)sizeof(T);
   static constexpr int FROW = TA + CE;
-  static constexpr int FST = COOP ? Lattices<DIM>::F::Q * TB * FROW * (int)sizeof(T) / 4 : Lattices<DIM>::F::Q * NT;
-  static constexpr int GST = Lattices<DIM>::G::Q * PLANE;
+  static constexpr int FST = COOP ? Lattices<DIM, LAT>::F::Q * TB * FROW * (int)sizeof(T) / 4
+                                  : Lattices<DIM, LAT>::F::Q * NT;
+  static constexpr int GST = Lattices<DIM, LAT>::G::Q * PLANE;
   // COOP refills a stage only after the next plane's barrier, so it keeps one
   // stage more in flight (Cahn-Hilliard tiles have no room for it).
   static constexpr int NST = (COOP && !CH) ? 4 : 3;
@@ -406,13 +427,13 @@ struct TileSmem {
 // kernel (one tile per block) and by the persistent batch kernel (tiles of
 // many domains claimed in turn). Accumulates the observables into obs.
 // ---------------------------------------------------------------------------
-template <int FAM, int DIM, typename T, int TA, int TB, int PAR = -1, int ROW = -1>
+template <int FAM, int DIM, typename T, int TA, int TB, int PAR = -1, int ROW = -1, int LAT = 0>
 __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, int c0, int chunk,
                                           float* __restrict__ s_phi, float* __restrict__ s_mu,
                                           float* __restrict__ s_stage, ObsPartial& obs) {
-  using LG = typename Lattices<DIM>::G;
-  using LF = typename Lattices<DIM>::F;
-  using LS = typename Lattices<DIM>::S;
+  using LG = typename Lattices<DIM, LAT>::G;
+  using LF = typename Lattices<DIM, LAT>::F;
+  using LS = typename Lattices<DIM, LAT>::S;
   constexpr int QG = LG::Q, QF = LF::Q, QS = LS::Q;
   constexpr int NT = TA * TB;
   constexpr bool CH = (FAM == FAM_LIANG);
@@ -430,7 +451,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
   // COOP: the block stages f together in 16-byte chunks (3D, rows aligned to
   // the population blocks, AA parity known at compile time).
   constexpr bool COOP = (DIM == 3) && (ROW == 1) && (PAR >= 0);
-  using SMEM = TileSmem<FAM, DIM, T, TA, TB, COOP>;
+  using SMEM = TileSmem<FAM, DIM, T, TA, TB, COOP, LAT>;
   constexpr bool STAGED = SMEM::STAGED;
   constexpr int FST = SMEM::FST, GST = SMEM::GST;
   constexpr int NST = SMEM::NST;
@@ -922,7 +943,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
       float gnew[QG];
 #pragma unroll
       for (int q = 0; q < QG; ++q) gnew[q] = g0[q];
-      Cell<FAM, DIM>::collide(P, gnew, f, pc, phis, gp, lp, mu_c, lmu, phiu, gamma, u, rho, p);
+      Cell<FAM, DIM, LAT>::collide(P, gnew, f, pc, phis, gp, lp, mu_c, lmu, phiu, gamma, u, rho, p);
 
       // Observables of the pre-collision state.
       {
@@ -1035,11 +1056,11 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
 // ---------------------------------------------------------------------------
 // The single-domain kernel: one tile per block.
 // ---------------------------------------------------------------------------
-template <int FAM, int DIM, typename T, int PAR, int ROW>
-__global__ void __launch_bounds__(Geom<FAM, DIM, T>::TA * Geom<FAM, DIM, T>::TB, Geom<FAM, DIM, T>::MINB)
+template <int FAM, int DIM, typename T, int PAR, int ROW, int LAT>
+__global__ void __launch_bounds__(Geom<FAM, DIM, T, LAT>::TA * Geom<FAM, DIM, T, LAT>::TB, Geom<FAM, DIM, T, LAT>::MINB)
 step_kernel(const StepArgs args) {
-  constexpr int TA = Geom<FAM, DIM, T>::TA, TB = Geom<FAM, DIM, T>::TB;
-  using SM = TileSmem<FAM, DIM, T, TA, TB, (DIM == 3) && (ROW == 1) && (PAR >= 0)>;
+  constexpr int TA = Geom<FAM, DIM, T, LAT>::TA, TB = Geom<FAM, DIM, T, LAT>::TB;
+  using SM = TileSmem<FAM, DIM, T, TA, TB, (DIM == 3) && (ROW == 1) && (PAR >= 0), LAT>;
   extern __shared__ __align__(16) float dyn_smem[];
   float* s_stage = dyn_smem;
   float* s_phi = dyn_smem + SM::STAGE;
@@ -1056,34 +1077,34 @@ step_kernel(const StepArgs args) {
     obs_zero_slot(args.obs_zero);
   ObsPartial obs;
   obs_init(obs);
-  step_tile<FAM, DIM, T, TA, TB, PAR, ROW>(args, ti * TA, tj * TB, bid * args.chunk, args.chunk, s_phi, s_mu,
-                                           s_stage, obs);
+  step_tile<FAM, DIM, T, TA, TB, PAR, ROW, LAT>(args, ti * TA, tj * TB, bid * args.chunk, args.chunk, s_phi, s_mu,
+                                                s_stage, obs);
   obs_block_commit(obs, args.obs_slot, s_red);
 }
 
-template <int FAM, int DIM, typename T, int PAR, int ROW>
+template <int FAM, int DIM, typename T, int PAR, int ROW, int LAT>
 void launch_step_par(const StepArgs& args, cudaStream_t stream) {
-  constexpr int TA = Geom<FAM, DIM, T>::TA, TB = Geom<FAM, DIM, T>::TB;
-  constexpr size_t smem = TileSmem<FAM, DIM, T, TA, TB, (DIM == 3) && (ROW == 1) && (PAR >= 0)>::BYTES;
+  constexpr int TA = Geom<FAM, DIM, T, LAT>::TA, TB = Geom<FAM, DIM, T, LAT>::TB;
+  constexpr size_t smem = TileSmem<FAM, DIM, T, TA, TB, (DIM == 3) && (ROW == 1) && (PAR >= 0), LAT>::BYTES;
   static const cudaError_t attr = cudaFuncSetAttribute(
-      step_kernel<FAM, DIM, T, PAR, ROW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      step_kernel<FAM, DIM, T, PAR, ROW, LAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   (void)attr;
   const int NA = args.p.nx, NB = (DIM == 3) ? args.p.ny : 1, NC = (DIM == 3) ? args.p.nz : args.p.ny;
   const long long tiles = (long long)((NA + TA - 1) / TA) * ((NB + TB - 1) / TB);
   const long long chunks = (NC + args.chunk - 1) / args.chunk;
   dim3 block(TA, TB, 1);
-  step_kernel<FAM, DIM, T, PAR, ROW><<<(unsigned)(tiles * chunks), block, smem, stream>>>(args);
+  step_kernel<FAM, DIM, T, PAR, ROW, LAT><<<(unsigned)(tiles * chunks), block, smem, stream>>>(args);
 }
 
-template <int FAM, int DIM, typename T>
+template <int FAM, int DIM, typename T, int LAT = 0>
 void launch_step(const StepArgs& args, cudaStream_t stream) {
   const bool row = args.p.nx % (int)kPopBlock == 0;
   if (args.parity) {
-    if (row) launch_step_par<FAM, DIM, T, 1, 1>(args, stream);
-    else launch_step_par<FAM, DIM, T, 1, 0>(args, stream);
+    if (row) launch_step_par<FAM, DIM, T, 1, 1, LAT>(args, stream);
+    else launch_step_par<FAM, DIM, T, 1, 0, LAT>(args, stream);
   } else {
-    if (row) launch_step_par<FAM, DIM, T, 0, 1>(args, stream);
-    else launch_step_par<FAM, DIM, T, 0, 0>(args, stream);
+    if (row) launch_step_par<FAM, DIM, T, 0, 1, LAT>(args, stream);
+    else launch_step_par<FAM, DIM, T, 0, 0, LAT>(args, stream);
   }
 }
 

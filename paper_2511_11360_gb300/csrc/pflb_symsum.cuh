@@ -112,4 +112,41 @@ template <> struct Sym<D3Q19> {
   }
 };
 
+// D3Q27: D3Q19's nineteen, then corners 19 (1,1,1) 20 (-1,-1,-1) 21 (1,1,-1)
+// 22 (-1,-1,1) 23 (1,-1,1) 24 (-1,1,-1) 25 (-1,1,1) 26 (1,-1,-1). With the
+// opposite-pair sums P1..P4 (19+20, 21+22, 23+24, 25+26), each mirror swaps
+// them in pairs (x: P1<->P4, P2<->P3; y: P1<->P3, P2<->P4; z: P1<->P2,
+// P3<->P4), all of which leave ((P1 + P2) + (P3 + P4)) bit for bit intact;
+// the first and mixed second moments use the matching pairings.
+template <> struct Sym<D3Q27> {
+  using B = Sym<D3Q19>;
+  template <typename V>
+  __device__ __forceinline__ static float corners(const V& v) {
+    return ((v[19] + v[20]) + (v[21] + v[22])) + ((v[23] + v[24]) + (v[25] + v[26]));
+  }
+  template <typename V>
+  __device__ __forceinline__ static float moving(const V& v) {
+    return B::moving(v) + corners(v);
+  }
+  template <typename V>
+  __device__ __forceinline__ static float first(const V& v, int k) {
+    float c;
+    if (k == 0) c = ((v[19] - v[20]) + (v[21] - v[22])) + ((v[23] - v[24]) + (v[26] - v[25]));
+    else if (k == 1) c = ((v[19] - v[20]) + (v[21] - v[22])) + ((v[24] - v[23]) + (v[25] - v[26]));
+    else c = ((v[19] - v[20]) + (v[22] - v[21])) + ((v[23] - v[24]) + (v[25] - v[26]));
+    return B::first(v, k) + c;
+  }
+  template <typename V>
+  __device__ __forceinline__ static float second(const V& v, int i, int j) {
+    if (i == j) return B::second(v, i, j) + corners(v);
+    const int a = i < j ? i : j, b = i < j ? j : i;
+    const float P1 = v[19] + v[20], P2 = v[21] + v[22], P3 = v[23] + v[24], P4 = v[25] + v[26];
+    float c;
+    if (a == 0 && b == 1) c = (P1 + P2) - (P3 + P4);
+    else if (a == 0 && b == 2) c = (P1 + P3) - (P2 + P4);
+    else c = (P1 + P4) - (P2 + P3);
+    return B::second(v, i, j) + c;
+  }
+};
+
 }  // namespace pflb

@@ -40,6 +40,8 @@ class Params(ctypes.Structure):
         ("gravity", ctypes.c_double * 3), ("force_density", ctypes.c_double * 3),
         ("lundgren_A", ctypes.c_double), ("wall_u", ctypes.c_double * 2),
         ("grad_eps", ctypes.c_double),
+        ("lattice_f", ctypes.c_int32), ("collision", ctypes.c_int32),
+        ("mrt_s_bulk", ctypes.c_double), ("mrt_s_ho", ctypes.c_double),
     ]
 
 
@@ -194,6 +196,10 @@ def make_params(d):
         p.gravity[k] = float(g[k]) if k < len(g) else 0.0
         p.force_density[k] = float(fd[k]) if k < len(fd) else 0.0
     p.wall_u[0], p.wall_u[1] = float(wu[0]), float(wu[1])
+    p.lattice_f = int(d.get("lattice_f", 0))   # 0: D2Q9 in 2D, D3Q19 in 3D
+    p.collision = int(d.get("collision", 0))
+    p.mrt_s_bulk = float(d.get("mrt_s_bulk", 1.0))
+    p.mrt_s_ho = float(d.get("mrt_s_ho", 1.0))
     return p
 
 

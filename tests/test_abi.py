@@ -38,10 +38,10 @@ def test_every_declared_symbol_is_exported(lib):
     assert declared <= set(pflb.SIGNATURES), declared - set(pflb.SIGNATURES)
 
 
-@pytest.mark.parametrize("dim,which", [(2, 0), (2, 1), (3, 0), (3, 1)])
+@pytest.mark.parametrize("dim,which", [(2, 0), (2, 1), (3, 0), (3, 1), (3, 2)])
 def test_lattice_tables_match_oracle(lib, dim, which):
     e, w = pflb.lattice(dim, which)
-    lat = O.lattices_for(dim)[which]
+    lat = O.D3Q27 if which == 2 else O.lattices_for(dim)[which]
     assert e.shape[0] == lat.Q
     assert np.array_equal(e[:, :dim], lat.e)
     assert np.allclose(w, lat.w, atol=1e-15)
@@ -51,6 +51,8 @@ def test_lattice_tables_match_oracle(lib, dim, which):
     dict(dim=4), dict(nx=0), dict(family=7), dict(storage=5), dict(nu_H=-0.2),
     dict(W=0.0), dict(phi_H=0.3, phi_L=0.3), dict(M=0.0), dict(obs_capacity=0),
     dict(dim=3, nz=8, bc_y=1), dict(visc_interp=9), dict(rho_L=0.0),
+    dict(lattice_f=27), dict(dim=3, nz=8, lattice_f=21), dict(dim=3, nz=8, collision=1),
+    dict(dim=3, nz=8, lattice_f=27, collision=1, mrt_s_ho=2.0), dict(dim=3, nz=8, collision=2),
 ])
 def test_invalid_parameters_are_rejected(lib, bad):
     d = cases.params(dim=2, nx=16, ny=12)

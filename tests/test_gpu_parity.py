@@ -52,6 +52,13 @@ def small_case(kind, fam):
         P, phi, u = C.droplet_in_tgv_3d(nx=35, ny=11, nz=9, R=4.0, W=3.0, family=fam)
         P.update(rho_H=2.0, rho_L=1.0, nu_L=0.05)
         return P, phi, u, 3
+    if kind == "3d_row":
+        # nx a multiple of the 32-cell population block: the block-staged
+        # path (ragged in y and z)
+        P, phi, u = C.droplet_in_tgv_3d(nx=64, ny=11, nz=9, R=4.0, W=3.0, family=fam,
+                                        centre=(0.3, 0.5, 0.5))
+        P.update(rho_H=2.0, rho_L=1.0, nu_L=0.05)
+        return P, phi, u, 3
     raise ValueError(kind)
 
 
@@ -80,6 +87,12 @@ def laminar_case(kind, fam):
                                         centre=(0.37, 0.58, 0.44), phase=(0.4, 1.1, 0.7))
         P.update(rho_H=2.0, rho_L=1.0, nu_L=0.05)
         return P, phi, u, 4
+    if kind == "3d_row":
+        # the same flow on a 32-aligned x extent (block-staged path)
+        P, phi, u = C.droplet_in_tgv_3d(nx=32, ny=20, nz=18, R=6.0, W=3.0, family=fam,
+                                        centre=(0.37, 0.58, 0.44), phase=(0.4, 1.1, 0.7))
+        P.update(rho_H=2.0, rho_L=1.0, nu_L=0.05)
+        return P, phi, u, 4
     raise ValueError(kind)
 
 
@@ -92,7 +105,7 @@ STORAGE_TOL = {0: 2e-6, 1: 1.5e-3, 2: 1.2e-2}   # relative to max |population|
 
 
 @pytest.mark.parametrize("storage", [0, 1, 2], ids=["fp32", "fp16", "bf16"])
-@pytest.mark.parametrize("kind", ["2d", "2d_walls", "2d_moving", "3d"])
+@pytest.mark.parametrize("kind", ["2d", "2d_walls", "2d_moving", "3d", "3d_row"])
 @pytest.mark.parametrize("fam", FAMS, ids=FID)
 def test_one_step_canonical_parity(fam, kind, storage):
     """Init and two steps (an even and an odd AA step): the GPU's canonical
@@ -117,7 +130,7 @@ def test_one_step_canonical_parity(fam, kind, storage):
 
 
 # ------------------------------------------------------- 1000-step parity
-@pytest.mark.parametrize("kind", ["2d", "2d_static", "2d_walls", "2d_moving", "3d"])
+@pytest.mark.parametrize("kind", ["2d", "2d_static", "2d_walls", "2d_moving", "3d", "3d_row"])
 @pytest.mark.parametrize("fam", FAMS, ids=FID)
 def test_laminar_1000_steps_fp32(fam, kind):
     """phi and u after 1000 steps within 1e-5 (relative L-infinity) of the FP64
@@ -266,7 +279,7 @@ def _mirror_state(P, blob, axis):
     cell index reversed along that axis, each population moved to the
     velocity with that component negated, phi*u component negated."""
     dim = P["dim"]
-    lg, lf, _ = O.lattices_for(dim)
+    lg, lf, _ = O.lattices_of(P)
     st = O.unpack_state(P, blob.astype(np.float64))
     ax = dim - 1 - axis
 
@@ -287,7 +300,8 @@ def _mirror_state(P, blob, axis):
 
 
 @pytest.mark.parametrize("fam", [C.FAKHARI2017, C.LIANG2014, C.LIANG2018], ids=["fakhari2017", "liang2014", "liang2018"])
-@pytest.mark.parametrize("kind,axis", [("2d", 0), ("2d_walls", 0), ("2d_walls", 1), ("3d", 0), ("3d", 2)])
+@pytest.mark.parametrize("kind,axis", [("2d", 0), ("2d_walls", 0), ("2d_walls", 1), ("3d", 0), ("3d", 2),
+                                       ("3d_row", 0), ("3d_row", 1)])
 def test_step_is_mirror_exact(fam, kind, axis):
     """The FP32 step commutes bit for bit with reflections of the domain: every
     velocity sum adds opposite pairs and mirror partners commutatively, so no
