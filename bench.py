@@ -13,7 +13,8 @@ W = 4, We = 5, density ratio 1, linear forcing, conservative Allen-Cahn
   roofline     algorithmic bytes/LU x cells / kernel time against the measured
                HBM copy bandwidth
   variants     FP16 / BF16 deviation storage of the same workload; the other
-               four families (Chai2018, Hu2019, Liang2014, Liang2018) on it; the
+               four families (Chai2018, Hu2019, Liang2014, Liang2018) on it;
+               D3Q27 hydrodynamics with the MRT collision on it; the
                batched form: 512 2D droplet-in-shear domains (sizes uniform in
                {64,128,256,512}^2, the four families mixed) in one persistent
                launch per step, autotuned launch shape, CUDA-graph replay;
@@ -441,6 +442,19 @@ def main():
                     "roofline_frac": b3 * cells / (t3 / args.steps) / 1e9 / peak,
                     "ms_per_step": t3 / args.steps * 1e3, "time_vs_fakhari2017": t3 / t}
             variants["families_%s" % args.storage] = fams
+            # The paper's own 3D hydrodynamics: D3Q27 with the MRT collision
+            # (Sec. IV; rates of Reading R20), same workload and family.
+            s4 = pflb.Sim(dict(P, storage=storage, obs_capacity=4, lattice_f=27, collision=1,
+                               mrt_s_bulk=1.0, mrt_s_ho=1.0), stream=torch.cuda.current_stream())
+            s4.init(phi, u)
+            b4 = s4.bytes_per_update()
+            t4 = _max_over_ranks(time_steps(s4, args.steps, args.warmup, world), world)
+            s4.close()
+            variants["d3q27_mrt_%s" % args.storage] = {
+                "value": cells * args.steps * world / t4 / 1e9, "unit": "GLUPS", "bytes_per_lu": b4,
+                "roofline_frac": b4 * cells / (t4 / args.steps) / 1e9 / peak,
+                "ms_per_step": t4 / args.steps * 1e3, "time_vs_d3q19_bgk": t4 / t,
+                "collision": "MRT, raw moments, s_bulk = s_ho = 1"}
         if not args.no_batched:
             variants["batched_2d_shear_512"] = batched_variant(args.steps, args.warmup, peak)
         if not args.no_adjoint:

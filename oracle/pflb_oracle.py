@@ -424,12 +424,14 @@ def mrt_collide(P, lat, f, feq, Fb, tau):
     mrt_s_ho. With both rates equal to 1/tau this is the BGK update."""
     M, ijk = mrt_moment_matrix(lat)
     Minv = np.linalg.inv(M)
+    # evaluate in the state's precision (float32 runs size the FP32 floor)
+    M, Minv = M.astype(f.dtype), Minv.astype(f.dtype)
     shape = f.shape[1:]
-    w = 1.0 / tau
+    w = (1.0 / tau).astype(f.dtype) if isinstance(tau, np.ndarray) else f.dtype.type(1.0 / tau)
     neq = np.tensordot(M, f - feq, axes=([1], [0]))       # (27, ...)
     mF = np.tensordot(M, Fb, axes=([1], [0]))
-    sb, sh = P["mrt_s_bulk"], P["mrt_s_ho"]
-    rate = np.empty((27,) + shape)
+    sb, sh = f.dtype.type(P["mrt_s_bulk"]), f.dtype.type(P["mrt_s_ho"])
+    rate = np.empty((27,) + shape, dtype=f.dtype)
     order = [i + j + k for (i, j, k) in ijk]
     for r, o in enumerate(order):
         rate[r] = w if o <= 2 else sh
