@@ -20,7 +20,9 @@ y = -1/2 and y = ny - 1/2 with halfway bounce-back (Reading R9).
 Families: FAKHARI2017 (conservative AC, Sec. II C 1), CHAI2018 (nonlocal AC,
 Sec. II C 3), HU2019 (hybrid AC, Sec. II C 4), LIANG2014 (Cahn-Hilliard,
 Sec. II D 1), LIANG2018 (conservative AC with the conservative form of the
-Navier-Stokes equations, Sec. II C 2).
+Navier-Stokes equations, Sec. II C 2), BAO2024 (Cahn-Hilliard with singular
+mobility, lattice kinetic scheme and quasi-incompressible Navier-Stokes,
+Sec. II D 3; periodic domains).
 
 Parity pins: tests/test_oracle_pins.py and tests/test_oracle_physics.py.
 """
@@ -30,7 +32,8 @@ import math
 import numpy as np
 
 __all__ = [
-    "FAKHARI2017", "CHAI2018", "HU2019", "LIANG2014", "LIANG2018", "FAMILY_NAMES",
+    "FAKHARI2017", "CHAI2018", "HU2019", "LIANG2014", "LIANG2018", "BAO2024", "FAMILY_NAMES",
+    "bao_mobility", "bao_rates", "quasi_theta", "geq_bao", "feq_bao", "source_yang", "force_yang",
     "Lattice", "D2Q9", "D3Q19", "D3Q27", "D3Q7", "lattices_for", "lattices_of",
     "mrt_moment_matrix", "mrt_collide",
     "default_params", "derived", "State",
@@ -43,9 +46,10 @@ __all__ = [
     "observables", "step_at_cells", "pack_state", "unpack_state",
 ]
 
-FAKHARI2017, CHAI2018, HU2019, LIANG2014, LIANG2018 = 0, 1, 2, 3, 4
+FAKHARI2017, CHAI2018, HU2019, LIANG2014, LIANG2018, BAO2024 = 0, 1, 2, 3, 4, 5
 FAMILY_NAMES = {FAKHARI2017: "fakhari2017", CHAI2018: "chai2018",
-                HU2019: "hu2019", LIANG2014: "liang2014", LIANG2018: "liang2018"}
+                HU2019: "hu2019", LIANG2014: "liang2014", LIANG2018: "liang2018",
+                BAO2024: "bao2024"}
 # Families that carry phi*u of the previous step for the backward-Euler
 # d_t(phi u) of Sec. III B.
 PHIU_FAMILIES = (LIANG2014, LIANG2018)
@@ -403,6 +407,87 @@ def force_liang2018(lat, u, grad_rho, F):
 
 
 # --------------------------------------------------------------------------
+# Bao2024: singular mobility, lattice kinetic scheme, quasi-incompressible NS
+# (Sec. II D 3, with the sources and updates of Yang2016, Sec. II D 2)
+# --------------------------------------------------------------------------
+def bao_mobility(P, phi):
+    """M = 4 M_0 |phi - phi_H| |phi - phi_L| / (phi_H - phi_L)^2, Eq.
+    (bao_singular_mobility); M_0 (the mobility at phi_0) is the parameter M."""
+    return 4.0 * P["M"] * np.abs(phi - P["phi_H"]) * np.abs(phi - P["phi_L"]) / (P["phi_H"] - P["phi_L"]) ** 2
+
+
+def bao_rates(P, cs2):
+    """Constant relaxation times of the lattice kinetic scheme (Reading R21):
+    tau_phi = M_0/(c_s^2 eta) + 1/2 and tau = max(nu_H, nu_L)/c_s^2 + 1/2, so
+    that A = tau_phi - 1/2 - M/(c_s^2 eta) and B = tau - 1/2 - nu/c_s^2 of
+    Eqs. (bao_Mphi), (bao_v) are >= 0 everywhere."""
+    tau_phi = P["M"] / (cs2 * P["eta_ch"]) + 0.5
+    tau = max(P["nu_H"], P["nu_L"]) / cs2 + 0.5
+    return tau_phi, tau
+
+
+def quasi_theta(P):
+    """theta = (rho_H/rho_L - 1)/(phi_H - phi_L rho_H/rho_L), Eq.
+    (quasi_incomp_system); the gamma of Eqs. (Yang_F), (yang_p_update)
+    (Reading R21)."""
+    r = P["rho_H"] / P["rho_L"]
+    return (r - 1.0) / (P["phi_H"] - P["phi_L"] * r)
+
+
+def _gamma_u(lat, u):
+    """Gamma_a(u) = w (e.u/c_s^2 + (e.u)^2/(2 c_s^4) - u.u/(2 c_s^2)), Eq. (Gamma_beta)."""
+    eu = _edot(lat, u)
+    cs2 = lat.cs2
+    w = lat.w.astype(u.dtype).reshape((-1,) + (1,) * (u.ndim - 1))
+    return w * (eu / cs2 + eu ** 2 / (2 * cs2 ** 2) - _udotu(u) / (2 * cs2))
+
+
+def geq_bao(lat, phi, u, mu, eta, A, grad_mu):
+    """Eq. (bao_g_eq): a = 0: phi - (1 - w_0) eta mu + phi Gamma_0 + w_0 A eta e_0.grad mu;
+    a != 0: w eta mu + phi Gamma_a + w A eta e_a.grad mu (dt = 1)."""
+    w = lat.w.astype(phi.dtype).reshape((-1,) + (1,) * phi.ndim)
+    out = w * eta * mu + phi * _gamma_u(lat, u) + w * A * eta * _edot(lat, grad_mu)
+    out[0] = phi - (1.0 - float(lat.w[0])) * eta * mu + phi * _gamma_u(lat, u)[0]
+    return out
+
+
+def feq_bao(lat, p, rho, u, B, S):
+    """Eq. (bao_f_eq): w p + c_s^2 rho Gamma(u) + 1/2 rho w B S:(e e - c_s^2 I),
+    S = grad u + (grad u)^T (dt = 1); S is a d x d nested list of fields."""
+    cs2 = lat.cs2
+    shp = (-1,) + (1,) * p.ndim
+    w = lat.w.astype(u.dtype).reshape(shp)
+    d = u.shape[0]
+    tr = sum(S[i][i] for i in range(d))
+    eeS = np.zeros((lat.Q,) + p.shape, dtype=u.dtype)
+    for i in range(d):
+        for j in range(d):
+            eeS += (lat.ef[:, i] * lat.ef[:, j]).astype(u.dtype).reshape(shp) * S[i][j]
+    return w * p + cs2 * rho * _gamma_u(lat, u) + 0.5 * rho * w * B * (eeS - cs2 * tr)
+
+
+def source_yang(lat, phi, rho, u, grad_p, F):
+    """Eq. (Yang_G): G = -phi/(c_s^2 rho) (e - u).(grad p - F) s_a(u), with
+    s_a = w + Gamma_a (Eq. Yang_Gamma)."""
+    V = grad_p - F
+    w = lat.w.astype(u.dtype).reshape((-1,) + (1,) * (u.ndim - 1))
+    s = w + _gamma_u(lat, u)
+    return -phi / (lat.cs2 * rho) * (_edot(lat, V) - np.sum(u * V, axis=0)) * s
+
+
+def force_yang(lat, rho, u, grad_rho, F, theta, divJ):
+    """Eq. (Yang_F): F_b = (e - u).[F s_b + Gamma_b c_s^2 grad rho]
+    - w c_s^2 rho theta div(M grad mu)."""
+    cs2 = lat.cs2
+    w = lat.w.astype(u.dtype).reshape((-1,) + (1,) * (u.ndim - 1))
+    Gam = _gamma_u(lat, u)
+    s = w + Gam
+    eF = _edot(lat, F) - np.sum(u * F, axis=0)
+    eg = _edot(lat, grad_rho) - np.sum(u * grad_rho, axis=0)
+    return eF * s + Gam * cs2 * eg - w * cs2 * rho * theta * divJ
+
+
+# --------------------------------------------------------------------------
 # Multiple-relaxation-time collision on D3Q27 (Sec. IV, Reading R20)
 # --------------------------------------------------------------------------
 def mrt_moment_matrix(lat):
@@ -511,6 +596,9 @@ def macroscopic(P, st, gamma=None):
     tau = nu / lf.cs2 + 0.5                        # Eq. (fakhari_tau_model), mu/rho = nu
     if fam == LIANG2014:
         tau_phi = P["M"] / (P["eta_ch"] * lg.cs2) + 0.5   # Sec. II D 1, tau_phi = M/(eta c_s^2) + 1/2
+    elif fam == BAO2024:
+        tau_phi, tau = bao_rates(P, lg.cs2)               # Reading R21 (constant)
+        tau = tau * np.ones_like(phi)
     else:
         tau_phi = P["M"] / lg.cs2 + 0.5                   # Eq. (fakhari_tau_model)
     m.update(rho=rho, nu=nu, tau=tau, tau_phi=tau_phi)
@@ -544,6 +632,34 @@ def macroscopic(P, st, gamma=None):
         p = lf.cs2 / (1.0 - w0) * (f[1:].sum(axis=0) + 0.5 * np.sum(u * grad_rho, axis=0)
                                    + rho * w0 * (-_udotu(u) / (2 * lf.cs2)))
         m.update(lap_mu=lap_mu, Fa=Fa, p=p, u=u, F=F, Fs=Fs, Fb=Fb + FL)
+        return m
+
+    if fam == BAO2024:
+        # Lattice kinetic scheme (Sec. II D 3): A and B of Eqs. (bao_Mphi),
+        # (bao_v) with the constant tau_phi, tau; updates of Eq. (yang_update).
+        cs2 = lf.cs2
+        eta = P["eta_ch"]
+        Mphi = bao_mobility(P, phi)
+        A_lks = tau_phi - 0.5 - Mphi / (cs2 * eta)
+        B_lks = tau - 0.5 - nu / cs2
+        grad_mu = gradient(mu, ls, walls)
+        lap_mu = laplacian(mu, ls, walls)
+        # div(M grad mu) = M lap mu + grad M . grad mu (Reading R21)
+        divJ = Mphi * lap_mu + np.sum(gradient(Mphi, ls, walls) * grad_mu, axis=0)
+        theta = quasi_theta(P)
+        # Eq. (yang_u_update): rho c_s^2 u = sum e f + c_s^2 F / 2, F = F_s + F_b
+        # (linear forcing A rho u solved for exactly)
+        u = (mom + 0.5 * cs2 * (Fs + Fb)) / (rho * cs2 * (1.0 - 0.5 * A))
+        FL = A * rho * u
+        F = Fs + Fb + FL
+        # Eq. (yang_p_update)
+        p = f.sum(axis=0) + 0.5 * cs2 * (np.sum(u * grad_rho, axis=0) - theta * rho * divJ)
+        d = P["dim"]
+        grad_u = [gradient(u[k], ls, walls) for k in range(d)]      # grad_u[k][i] = d_i u_k
+        S = [[grad_u[j][i] + grad_u[i][j] for j in range(d)] for i in range(d)]
+        m.update(tau=tau, tau_phi=tau_phi, Mphi=Mphi, A_lks=A_lks, B_lks=B_lks, grad_mu=grad_mu,
+                 lap_mu=lap_mu, divJ=divJ, theta=theta, p=p, u=u, F=F, Fs=Fs, Fb=Fb + FL,
+                 grad_p=gradient(p, ls, walls), S=S)
         return m
 
     if fam == LIANG2018:
@@ -615,6 +731,9 @@ def collide(P, st, m):
         dtphiu = phiu_new - st.phiu_prev                      # backward Euler, Sec. III B
         w = lg.w.astype(phi.dtype).reshape((-1,) + (1,) * phi.ndim)
         G = w * _edot(lg, dtphiu) / lg.cs2 + source_conservative(P, lg, phi, m["grad_phi"])  # Eq. (liang_G_final)
+    elif fam == BAO2024:
+        geq = geq_bao(lg, phi, u, m["mu"], P["eta_ch"], m["A_lks"], m["grad_mu"])   # Eq. (bao_g_eq)
+        G = source_yang(lg, phi, rho, u, m["grad_p"], m["F"])                       # Eq. (Yang_G)
     elif fam == LIANG2014:
         geq = geq_liang2014(lg, phi, u, m["mu"], P["eta_ch"])
         phiu_new = phi * u
@@ -634,6 +753,9 @@ def collide(P, st, m):
     elif fam == LIANG2018:
         feq = feq_pressure(lf, m["p"], rho, u)                 # Eq. (liang_feq)
         Fb = force_liang2018(lf, u, m["grad_rho"], m["F"])
+    elif fam == BAO2024:
+        feq = feq_bao(lf, m["p"], rho, u, m["B_lks"], m["S"])                         # Eq. (bao_f_eq)
+        Fb = force_yang(lf, rho, u, m["grad_rho"], m["F"], m["theta"], m["divJ"])     # Eq. (Yang_F)
     else:
         feq = feq_velocity(lf, m["p"] / (rho * lf.cs2), u)
         if fam == FAKHARI2017:
@@ -704,6 +826,21 @@ def init_state(P, phi0, u0, dtype=np.float64):
     elif fam == LIANG2018:
         g = geq_chai(lg, phi0, u0)
         phiu = phi0 * u0
+    elif fam == BAO2024:
+        # Equilibria of Eqs. (bao_g_eq), (bao_f_eq) with p = 0 (Reading R8).
+        c = derived(P)
+        walls = _walls(P)
+        mu = 4.0 * c["beta"] * (phi0 - P["phi_H"]) * (phi0 - P["phi_L"]) * (phi0 - c["phi0"]) \
+            - c["kappa"] * laplacian(phi0, ls, walls)
+        tau_phi, tau = bao_rates(P, lg.cs2)
+        A_lks = tau_phi - 0.5 - bao_mobility(P, phi0) / (lg.cs2 * P["eta_ch"])
+        g = geq_bao(lg, phi0, u0, mu, P["eta_ch"], A_lks, gradient(mu, ls, walls))
+        d = P["dim"]
+        grad_u = [gradient(u0[k], ls, walls) for k in range(d)]
+        S = [[grad_u[j][i] + grad_u[i][j] for j in range(d)] for i in range(d)]
+        B_lks = tau - 0.5 - kinematic_viscosity(P, phi0, rho) / lf.cs2
+        f = feq_bao(lf, np.zeros_like(rho), rho, u0, B_lks, S)
+        return State(g, f, None, 0)
     else:
         c = derived(P)
         mu = 4.0 * c["beta"] * (phi0 - P["phi_H"]) * (phi0 - P["phi_L"]) * (phi0 - c["phi0"]) \
@@ -726,7 +863,7 @@ def step(P, st, gamma=None):
         g_new = st.g.copy()               # Sec. III D: phase-field evolution disabled
     else:
         g_new = stream(P, lg, gs, m["phi"])
-    f_scale = m["rho"] if P["family"] in (LIANG2014, LIANG2018) else np.ones_like(m["rho"])
+    f_scale = m["rho"] if P["family"] in (LIANG2014, LIANG2018, BAO2024) else np.ones_like(m["rho"])
     f_new = stream(P, lf, fs, f_scale)
     return State(g_new, f_new, phiu_new, st.t + 1)
 
@@ -772,7 +909,8 @@ def step_at_cells(P, st, cells, gamma=None):
 
     ``cells`` is a list of (x, y[, z]). Each output depends only on stored
     populations within Chebyshev radius 2 (3 for Liang2014, whose mu needs a
-    second stencil), so each is computed on a periodic patch of that radius
+    second stencil; 4 for Bao2024, whose pressure gradient acts on the
+    stencils of mu), so each is computed on a periodic patch of that radius
     around the cell; the patch border is wrong after the step but the centre
     is not. For Chai2018/Hu2019 the global gamma of the full domain must be
     passed in. Requires periodic boundaries.
@@ -781,7 +919,7 @@ def step_at_cells(P, st, cells, gamma=None):
     fam = P["family"]
     if fam in (CHAI2018, HU2019):
         assert gamma is not None
-    r = 3 if fam == LIANG2014 else 2
+    r = {LIANG2014: 3, BAO2024: 4}.get(fam, 2)   # Bao2024: grad p of div(M grad mu) (3) + streaming
     n = 2 * r + 1
     d = P["dim"]
     shape = _shape(P)
