@@ -56,10 +56,18 @@ typedef enum pflb_family {
   PFLB_NLAC_CHAI2018 = 1,   /* nonlocal Allen-Cahn, Sec. II C 3 */
   PFLB_HAC_HU2019 = 2,      /* hybrid Allen-Cahn with global weight lambda, Sec. II C 4 */
   PFLB_CH_LIANG2014 = 3,    /* Cahn-Hilliard with incompressible NS, Sec. II D 1 */
-  PFLB_CAC_LIANG2018 = 4    /* conservative Allen-Cahn with the conservative NS form:
+  PFLB_CAC_LIANG2018 = 4,   /* conservative Allen-Cahn with the conservative NS form:
                                first-order g_eq, pressure-based f_eq, d_t(phi u) in G,
                                Sec. II C 2 (Eqs. liang_geq, liang_feq, liang_G_final,
                                liang_F_final, liang_velocity_update, liang_p_update) */
+  PFLB_CH_BAO2024 = 5       /* Cahn-Hilliard with singular mobility M = 4 M_0 |phi - phi_H|
+                               |phi - phi_L| / (phi_H - phi_L)^2 (M_0 = params.M), lattice
+                               kinetic scheme and quasi-incompressible NS, Sec. II D 3
+                               (Eqs. bao_g_eq, bao_f_eq, bao_Mphi, bao_v, Yang_G, Yang_F,
+                               yang_update). Constant tau_phi = M_0/(c_s^2 eta) + 1/2 and
+                               tau = max(nu_H, nu_L)/c_s^2 + 1/2. Periodic domains, FP32
+                               storage, D2Q9 / D3Q19 + D3Q7; stepped by four passes
+                               (phi, mu, u and p, collision) instead of the fused kernel */
 } pflb_family;
 
 /* Population storage in device memory. Arithmetic is always FP32. The 16-bit

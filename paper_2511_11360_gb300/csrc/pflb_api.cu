@@ -70,7 +70,11 @@ int validate(const pflb_params* p, char* msg, size_t n) {
   const long long qmax = p->dim == 2 ? 9 : 19;
   if (((N + 31) / 32) * 32 * qmax >= (1LL << 32))
     return snprintf(msg, n, "Q * cells must be < 2^32 (%lld cells max)", ((1LL << 32) - 1) / qmax / 32 * 32), PFLB_EINVAL;
-  if (p->family < 0 || p->family > 4) return snprintf(msg, n, "unknown family %d", p->family), PFLB_EINVAL;
+  if (p->family < 0 || p->family > 5) return snprintf(msg, n, "unknown family %d", p->family), PFLB_EINVAL;
+  if (p->family == PFLB_CH_BAO2024 && (p->storage != PFLB_FP32 || p->bc_y != 0 || p->lattice_f == 27 ||
+                                       p->collision != 0))
+    return snprintf(msg, n, "Bao2024 runs on periodic domains with FP32 storage and BGK on D2Q9 / D3Q19"),
+           PFLB_EINVAL;
   if (p->storage < 0 || p->storage > 2) return snprintf(msg, n, "unknown storage %d", p->storage), PFLB_EINVAL;
   if (p->bc_y < 0 || p->bc_y > 2) return snprintf(msg, n, "bc_y must be 0, 1 or 2"), PFLB_EINVAL;
   if (p->bc_y != 0 && p->dim != 2) return snprintf(msg, n, "walls are supported in 2D only"), PFLB_EINVAL;
@@ -84,7 +88,7 @@ int validate(const pflb_params* p, char* msg, size_t n) {
   if (!(p->rho_H > 0.0 && p->rho_L > 0.0)) return snprintf(msg, n, "densities must be > 0"), PFLB_EINVAL;
   if (!(tau_of(p->nu_H) > 0.5 && tau_of(p->nu_L) > 0.5))
     return snprintf(msg, n, "tau = 3 nu + 1/2 must exceed 1/2 in both phases"), PFLB_EINVAL;
-  const double eta = p->family == 3 ? p->eta_ch : 1.0;
+  const double eta = (p->family == 3 || p->family == 5) ? p->eta_ch : 1.0;
   if (!(eta > 0.0)) return snprintf(msg, n, "eta must be > 0"), PFLB_EINVAL;
   if (!(3.0 * p->M / eta + 0.5 > 0.5)) return snprintf(msg, n, "tau_phi must exceed 1/2 (M > 0)"), PFLB_EINVAL;
   if (!(p->lundgren_A < 2.0)) return snprintf(msg, n, "lundgren_A must be < 2"), PFLB_EINVAL;
@@ -131,7 +135,7 @@ DevParams derive(const pflb_params* p) {
   d.four_beta_over_kappa = (float)(kappa > 0 ? 4.0 * beta / kappa : 32.0 / (p->W * p->W * dphi * dphi));
   d.counter_k = (float)(4.0 / (p->W * std::fabs(dphi)));  // sqrt(2 beta / kappa)
   d.M = (float)p->M;
-  const double eta = p->family == 3 ? p->eta_ch : 1.0;
+  const double eta = (p->family == 3 || p->family == 5) ? p->eta_ch : 1.0;
   const double tau_phi = 3.0 * p->M / eta + 0.5;                                   // Eq. (fakhari_tau_model)
   d.inv_tau_phi = (float)(1.0 / tau_phi);
   d.src_w_phi = (float)(1.0 - 0.5 / tau_phi);
@@ -150,6 +154,10 @@ DevParams derive(const pflb_params* p) {
   d.mrt = p->collision == 1 ? 1 : 0;
   d.mrt_sb = (float)p->mrt_s_bulk;
   d.mrt_sh = (float)p->mrt_s_ho;
+  // Bao2024 (Reading R21): theta of Eq. (quasi_incomp_system), constant tau.
+  const double r = p->rho_H / p->rho_L;
+  d.theta = (float)((r - 1.0) / (p->phi_H - p->phi_L * r));
+  d.lks_itau = (float)(1.0 / (3.0 * (p->nu_H > p->nu_L ? p->nu_H : p->nu_L) + 0.5));
   return d;
 }
 
@@ -159,7 +167,8 @@ void step_launch(int fam, int dim, int storage, const StepArgs& a, cudaStream_t 
     case 1: step_chai(dim, storage, a, s); break;
     case 2: step_hu(dim, storage, a, s); break;
     case 3: step_liang2014(dim, storage, a, s); break;
-    default: step_liang2018(dim, storage, a, s); break;
+    case 4: step_liang2018(dim, storage, a, s); break;
+    default: step_bao2024(dim, storage, a, s); break;
   }
 }
 
@@ -169,7 +178,8 @@ void init_launch(int fam, int dim, int storage, const InitArgs& a, cudaStream_t 
     case 1: init_chai(dim, storage, a, s); break;
     case 2: init_hu(dim, storage, a, s); break;
     case 3: init_liang2014(dim, storage, a, s); break;
-    default: init_liang2018(dim, storage, a, s); break;
+    case 4: init_liang2018(dim, storage, a, s); break;
+    default: init_bao2024(dim, storage, a, s); break;
   }
 }
 
@@ -212,6 +222,7 @@ StepArgs pflb::handle_step_args(const pflb_handle* h) {
   a.g_dst = h->g[1 - h->cur];
   a.f = h->f;
   a.phiu = h->phiu;
+  a.work = h->work;
   a.parity = (int)(h->step & 1);
   a.chunk = h->chunk > 0 ? h->chunk : default_chunk(h);
   a.N = h->N;
@@ -268,7 +279,7 @@ int pflb::handle_canon(pflb_handle* h, float* state_dev, int to_canon) {
   a.state = state_dev;
   a.parity = (int)(h->step & 1);
   a.to_canon = to_canon;
-  a.ch = h->family == 3;
+  a.ch = h->family == 3 || h->family == 5;   // Cahn-Hilliard: the D3Q7 rest population is stored
   a.N = h->N;
   canon_copy(h->dim, h->storage, a, h->stream);
   CU(h, cudaGetLastError());
@@ -324,6 +335,8 @@ int pflb_create(const pflb_params* params, void* cuda_stream, pflb_handle** out)
   if ((rc = alloc(&h->g[1], (size_t)h->QG * npad * h->elem + 16))) return rc;
   if ((rc = alloc(&h->f, (size_t)h->QF * npad * h->elem + 16))) return rc;
   if (fam_phiu(h->family) && (rc = alloc((void**)&h->phiu, (size_t)h->dim * h->N * sizeof(float)))) return rc;
+  if (h->family == PFLB_CH_BAO2024 && (rc = alloc((void**)&h->work, (size_t)(3 + h->dim) * h->N * sizeof(float))))
+    return rc;
   if ((rc = alloc((void**)&h->obs, (size_t)(h->obs_cap + 1) * sizeof(DevObs)))) return rc;
   if ((rc = alloc((void**)&h->gamma_acc, 6 * sizeof(double)))) return rc;
   return PFLB_OK;
@@ -345,6 +358,7 @@ int pflb_init(pflb_handle* h, const float* phi0, const float* u0) {
   a.f = h->f;
   a.phiu = h->phiu;
   a.N = h->N;
+  a.work = h->work;
   init_launch(h->family, h->dim, h->storage, a, h->stream);
   CU(h, cudaGetLastError());
   // Zero every observables slot and the nonlocal accumulators.
@@ -512,8 +526,14 @@ double pflb_bytes_per_update(const pflb_handle* h) {
   if (!h) return 0.0;
   // Stored populations read once and written once (the D3Q7 rest slot of the
   // Allen-Cahn families is identically zero and never touched).
-  const int qg = (h->dim == 3 && h->family != 3) ? h->QG - 1 : h->QG;
+  const int qg = (h->dim == 3 && h->family != 3 && h->family != 5) ? h->QG - 1 : h->QG;
   double b = 2.0 * (qg + h->QF) * (double)h->elem;
+  if (h->family == PFLB_CH_BAO2024) {
+    // the passes: g read for phi, phi and mu written and read by the mu,
+    // macroscopic and collision passes, f read for u and p, u and p written
+    // and read (field words of 4 bytes)
+    b += 4.0 * (qg + 1) + 8.0 + 4.0 * h->QF + 8.0 + 4.0 * (h->dim + 1) + 4.0 * (3 + h->dim);
+  }
   if (fam_phiu(h->family)) b += 2.0 * h->dim * 4.0;  // phi*u read + write
   if (handle_nonlocal(h)) b += (double)qg * h->elem;         // g read by the gamma reduction
   return b;
@@ -552,6 +572,7 @@ int pflb_destroy(pflb_handle* h) {
   cudaFree(h->g[1]);
   cudaFree(h->f);
   cudaFree(h->phiu);
+  cudaFree(h->work);
   cudaFree(h->obs);
   cudaFree(h->gamma_acc);
   cudaFree(h->scratch);

@@ -445,6 +445,8 @@ int pflb_batch_create(const pflb_params* params, int32_t n, void* cuda_stream, p
   for (int i = 0; i < n; ++i) {
     if (params[i].dim != 2) return bfail(b, PFLB_EINVAL, "domain %d: the batched step is 2D only", i);
     if (params[i].storage != PFLB_FP32) return bfail(b, PFLB_EINVAL, "domain %d: the batched step needs FP32 storage", i);
+    if (params[i].family > PFLB_CAC_LIANG2018)
+      return bfail(b, PFLB_EINVAL, "domain %d: the batched step runs the fused-kernel families (0..4)", i);
   }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {

@@ -16,6 +16,7 @@ constexpr int FAM_CHAI = 1;
 constexpr int FAM_HU = 2;
 constexpr int FAM_LIANG = 3;     // Liang2014 (Cahn-Hilliard)
 constexpr int FAM_LIANG18 = 4;   // Liang2018 (conservative Allen-Cahn, conservative NS form)
+constexpr int FAM_BAO = 5;       // Bao2024 (Cahn-Hilliard, singular mobility, multi-pass step)
 
 // Families that keep phi*u of the previous step for d_t(phi u) (Sec. III B)
 // and use the pressure-based hydrodynamic equilibrium (Eq. liang2_feq).
@@ -182,6 +183,8 @@ struct DevParams {
   int32_t lat;              // 3D hydrodynamic lattice: 0 D3Q19, 1 D3Q27
   int32_t mrt;              // 1: multiple-relaxation-time collision (D3Q27)
   float mrt_sb, mrt_sh;     // MRT rates: trace of the second moments, orders >= 3
+  float theta;              // Bao2024: quasi-incompressible theta (Eq. quasi_incomp_system)
+  float lks_itau;           // Bao2024: 1 / tau of the lattice kinetic scheme (constant)
 };
 
 // Observables accumulated by one pass (one slot of the per-step ring).

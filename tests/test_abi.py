@@ -53,6 +53,7 @@ def test_lattice_tables_match_oracle(lib, dim, which):
     dict(dim=3, nz=8, bc_y=1), dict(visc_interp=9), dict(rho_L=0.0),
     dict(lattice_f=27), dict(dim=3, nz=8, lattice_f=21), dict(dim=3, nz=8, collision=1),
     dict(dim=3, nz=8, lattice_f=27, collision=1, mrt_s_ho=2.0), dict(dim=3, nz=8, collision=2),
+    dict(family=5, storage=1), dict(family=5, bc_y=1), dict(family=5, dim=3, nz=8, lattice_f=27),
 ])
 def test_invalid_parameters_are_rejected(lib, bad):
     d = cases.params(dim=2, nx=16, ny=12)
@@ -78,7 +79,7 @@ def test_no_device_is_an_error_not_a_fallback(lib):
     assert ei.value.code == pflb.PFLB_ECUDA
 
 
-@pytest.mark.parametrize("bad", [dict(dim=3, nz=8), dict(storage=1), dict(storage=2)])
+@pytest.mark.parametrize("bad", [dict(dim=3, nz=8), dict(storage=1), dict(storage=2), dict(family=5)])
 def test_batch_rejects_unsupported_domains(lib, bad):
     good = cases.params(dim=2, nx=16, ny=12)
     d = dict(good)
