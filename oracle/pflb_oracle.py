@@ -22,7 +22,8 @@ Sec. II C 3), HU2019 (hybrid AC, Sec. II C 4), LIANG2014 (Cahn-Hilliard,
 Sec. II D 1), LIANG2018 (conservative AC with the conservative form of the
 Navier-Stokes equations, Sec. II C 2), BAO2024 (Cahn-Hilliard with singular
 mobility, lattice kinetic scheme and quasi-incompressible Navier-Stokes,
-Sec. II D 3; periodic domains).
+Sec. II D 3; periodic domains), LIU2023 (hybrid AC with the weight lambda(x)
+of a reinitialised signed distance, Sec. II C 5; periodic domains).
 
 Parity pins: tests/test_oracle_pins.py and tests/test_oracle_physics.py.
 """
@@ -32,7 +33,8 @@ import math
 import numpy as np
 
 __all__ = [
-    "FAKHARI2017", "CHAI2018", "HU2019", "LIANG2014", "LIANG2018", "BAO2024", "FAMILY_NAMES",
+    "FAKHARI2017", "CHAI2018", "HU2019", "LIANG2014", "LIANG2018", "BAO2024", "LIU2023", "FAMILY_NAMES",
+    "liu_psi_predictor", "liu_reinit_step", "liu_reinit", "liu_weight", "liu_gamma",
     "bao_mobility", "bao_rates", "quasi_theta", "geq_bao", "feq_bao", "source_yang", "force_yang",
     "Lattice", "D2Q9", "D3Q19", "D3Q27", "D3Q7", "lattices_for", "lattices_of",
     "mrt_moment_matrix", "mrt_collide",
@@ -46,13 +48,13 @@ __all__ = [
     "observables", "step_at_cells", "pack_state", "unpack_state",
 ]
 
-FAKHARI2017, CHAI2018, HU2019, LIANG2014, LIANG2018, BAO2024 = 0, 1, 2, 3, 4, 5
+FAKHARI2017, CHAI2018, HU2019, LIANG2014, LIANG2018, BAO2024, LIU2023 = 0, 1, 2, 3, 4, 5, 6
 FAMILY_NAMES = {FAKHARI2017: "fakhari2017", CHAI2018: "chai2018",
                 HU2019: "hu2019", LIANG2014: "liang2014", LIANG2018: "liang2018",
-                BAO2024: "bao2024"}
+                BAO2024: "bao2024", LIU2023: "liu2023"}
 # Families that carry phi*u of the previous step for the backward-Euler
 # d_t(phi u) of Sec. III B.
-PHIU_FAMILIES = (LIANG2014, LIANG2018)
+PHIU_FAMILIES = (LIANG2014, LIANG2018, LIU2023)
 
 CS2 = 1.0 / 3.0
 
@@ -275,6 +277,63 @@ def nonlocal_R(P, phi, gamma):
     return P["M"] * (-4.0 * c["beta"] / c["kappa"] * (phi - P["phi_H"]) * (phi - P["phi_L"])
                      * (phi - c["phi0"])
                      + gamma * (P["phi_H"] - phi) * (phi - P["phi_L"]))
+
+
+# --------------------------------------------------------------------------
+# Liu2023: the weight lambda(x) from a reinitialised signed distance
+# (Sec. II C 5, Reading R22)
+# --------------------------------------------------------------------------
+def liu_psi_predictor(P, phi):
+    """Predictor: psi = -(xi/4) ln((phi_H - phi_L)/(phi - phi_L) - 1), with phi
+    clamped to [phi_L + 0.01, phi_H - 0.01] (the three cases of the paper's
+    predictor). For the tanh profile it is the signed distance (> 0 in the
+    heavy phase), capped at (xi/4) ln 99 = 1.149 xi."""
+    lo, hi = P["phi_L"] + 0.01, P["phi_H"] - 0.01
+    pc = np.clip(phi, lo, hi)
+    return -0.25 * P["W"] * np.log((P["phi_H"] - P["phi_L"]) / (pc - P["phi_L"]) - 1.0)
+
+
+def liu_reinit_step(psi, psi0, dtau):
+    """One pseudo-time step of d psi/dt' + S(psi0)(|grad psi| - 1) = 0, S(psi0)
+    = psi0 / sqrt(psi0^2 + dx^2) (dx = 1), by the first-order Godunov upwind
+    scheme (Reading R22), periodic."""
+    S = psi0 / np.sqrt(psi0 * psi0 + 1.0)
+    g2p = np.zeros_like(psi)   # for S > 0
+    g2m = np.zeros_like(psi)   # for S < 0
+    for ax in range(psi.ndim):
+        dm = psi - np.roll(psi, 1, axis=ax)     # backward difference
+        dp = np.roll(psi, -1, axis=ax) - psi    # forward difference
+        g2p += np.maximum(np.maximum(dm, 0.0) ** 2, np.minimum(dp, 0.0) ** 2)
+        g2m += np.maximum(np.minimum(dm, 0.0) ** 2, np.maximum(dp, 0.0) ** 2)
+    grad = np.where(S > 0, np.sqrt(g2p), np.sqrt(g2m))
+    return psi - dtau * S * (grad - 1.0)
+
+
+def liu_reinit(P, phi):
+    """Corrector: n = ceil(2 d_min) steps of dt' = 1/2 from the predictor,
+    enough for the distance to travel past d_min = 3 xi (Reading R22)."""
+    psi0 = liu_psi_predictor(P, phi)
+    psi = psi0.copy()
+    for _ in range(int(math.ceil(2.0 * 3.0 * P["W"]))):
+        psi = liu_reinit_step(psi, psi0, 0.5)
+    return psi
+
+
+def liu_weight(P, psi):
+    """lambda = 1 where |psi| < d_min = 3 xi (interface band), 0 elsewhere."""
+    return (np.abs(psi) < 3.0 * P["W"]).astype(psi.dtype)
+
+
+def liu_gamma(P, phi, lam):
+    """gamma(t) of the nonlocal part, restricted to where it acts: the
+    (1 - lambda)-weighted integrals of Eq. (lagrange_multiplier), so that
+    sum (1 - lambda) R = 0 and sum phi is conserved (Reading R22)."""
+    c = derived(P)
+    wgt = 1.0 - lam
+    I1 = np.sum(wgt * 4.0 * c["beta"] / c["kappa"] * (phi - P["phi_H"]) * (phi - P["phi_L"])
+                * (phi - c["phi0"]))
+    I2 = np.sum(wgt * (P["phi_H"] - phi) * (phi - P["phi_L"]))
+    return I1 / I2 if I2 != 0.0 else 0.0
 
 
 # --------------------------------------------------------------------------
@@ -587,6 +646,16 @@ def macroscopic(P, st, gamma=None):
         lam = P["lambda_hybrid"] if fam == HU2019 else 0.0
         phi = phi_star + 0.5 * (1.0 - lam) * R
         m["gamma"], m["R"], m["lam"] = gamma, R, lam
+    elif fam == LIU2023:
+        # lambda(x) of the reinitialised signed distance of phi*, gamma over the
+        # lambda = 0 region, phi = phi* + (1 - lambda) R(phi*)/2 (as Reading R5,
+        # with the local weight; Reading R22).
+        lam = liu_weight(P, liu_reinit(P, phi_star))
+        if gamma is None:
+            gamma = liu_gamma(P, phi_star, lam)
+        R = nonlocal_R(P, phi_star, gamma)
+        phi = phi_star + 0.5 * (1.0 - lam) * R
+        m["gamma"], m["R"], m["lam"] = gamma, R, lam
     else:
         phi = phi_star
     m["phi"] = phi
@@ -662,7 +731,7 @@ def macroscopic(P, st, gamma=None):
                  grad_p=gradient(p, ls, walls), S=S)
         return m
 
-    if fam == LIANG2018:
+    if fam in (LIANG2018, LIU2023):
         # Eq. (liang_velocity_update), rho u = sum e f + F dt/2 with
         # F = F_s + F_b; the linear forcing A rho u is solved for exactly.
         u = (mom + 0.5 * (Fs + Fb)) / (rho * (1.0 - 0.5 * A))
@@ -731,6 +800,14 @@ def collide(P, st, m):
         dtphiu = phiu_new - st.phiu_prev                      # backward Euler, Sec. III B
         w = lg.w.astype(phi.dtype).reshape((-1,) + (1,) * phi.ndim)
         G = w * _edot(lg, dtphiu) / lg.cs2 + source_conservative(P, lg, phi, m["grad_phi"])  # Eq. (liang_G_final)
+    elif fam == LIU2023:
+        geq = geq_chai(lg, phi, u)                            # Liang2018's Eq. (liang_geq)
+        phiu_new = phi * u
+        dtphiu = phiu_new - st.phiu_prev
+        w = lg.w.astype(phi.dtype).reshape((-1,) + (1,) * phi.ndim)
+        lam = m["lam"]
+        G = lam * (w * _edot(lg, dtphiu) / lg.cs2 + source_conservative(P, lg, phi, m["grad_phi"])) \
+            + (1.0 - lam) * w * m["R"]                         # Eq. (Liu_G)
     elif fam == BAO2024:
         geq = geq_bao(lg, phi, u, m["mu"], P["eta_ch"], m["A_lks"], m["grad_mu"])   # Eq. (bao_g_eq)
         G = source_yang(lg, phi, rho, u, m["grad_p"], m["F"])                       # Eq. (Yang_G)
@@ -750,9 +827,9 @@ def collide(P, st, m):
     if fam == LIANG2014:
         feq = feq_pressure(lf, m["p"], rho, u)
         Fb = force_liang2014(lf, u, m["grad_rho"], m["F"])
-    elif fam == LIANG2018:
+    elif fam in (LIANG2018, LIU2023):
         feq = feq_pressure(lf, m["p"], rho, u)                 # Eq. (liang_feq)
-        Fb = force_liang2018(lf, u, m["grad_rho"], m["F"])
+        Fb = force_liang2018(lf, u, m["grad_rho"], m["F"])     # Eqs. (liang_F_final), (Liu_F)
     elif fam == BAO2024:
         feq = feq_bao(lf, m["p"], rho, u, m["B_lks"], m["S"])                         # Eq. (bao_f_eq)
         Fb = force_yang(lf, rho, u, m["grad_rho"], m["F"], m["theta"], m["divJ"])     # Eq. (Yang_F)
@@ -823,7 +900,7 @@ def init_state(P, phi0, u0, dtype=np.float64):
         g = geq_fakhari(lg, phi0, u0)
     elif fam in (CHAI2018, HU2019):
         g = geq_chai(lg, phi0, u0)
-    elif fam == LIANG2018:
+    elif fam in (LIANG2018, LIU2023):
         g = geq_chai(lg, phi0, u0)
         phiu = phi0 * u0
     elif fam == BAO2024:
@@ -847,7 +924,7 @@ def init_state(P, phi0, u0, dtype=np.float64):
             - c["kappa"] * laplacian(phi0, ls, _walls(P))
         g = geq_liang2014(lg, phi0, u0, mu, P["eta_ch"])
         phiu = phi0 * u0
-    if fam in (LIANG2014, LIANG2018):
+    if fam in (LIANG2014, LIANG2018, LIU2023):
         f = feq_pressure(lf, np.zeros_like(rho), rho, u0)
     else:
         f = feq_velocity(lf, np.zeros_like(rho), u0)
@@ -863,7 +940,7 @@ def step(P, st, gamma=None):
         g_new = st.g.copy()               # Sec. III D: phase-field evolution disabled
     else:
         g_new = stream(P, lg, gs, m["phi"])
-    f_scale = m["rho"] if P["family"] in (LIANG2014, LIANG2018, BAO2024) else np.ones_like(m["rho"])
+    f_scale = m["rho"] if P["family"] in (LIANG2014, LIANG2018, BAO2024, LIU2023) else np.ones_like(m["rho"])
     f_new = stream(P, lf, fs, f_scale)
     return State(g_new, f_new, phiu_new, st.t + 1)
 
