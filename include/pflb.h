@@ -60,7 +60,7 @@ typedef enum pflb_family {
                                first-order g_eq, pressure-based f_eq, d_t(phi u) in G,
                                Sec. II C 2 (Eqs. liang_geq, liang_feq, liang_G_final,
                                liang_F_final, liang_velocity_update, liang_p_update) */
-  PFLB_CH_BAO2024 = 5       /* Cahn-Hilliard with singular mobility M = 4 M_0 |phi - phi_H|
+  PFLB_CH_BAO2024 = 5,      /* Cahn-Hilliard with singular mobility M = 4 M_0 |phi - phi_H|
                                |phi - phi_L| / (phi_H - phi_L)^2 (M_0 = params.M), lattice
                                kinetic scheme and quasi-incompressible NS, Sec. II D 3
                                (Eqs. bao_g_eq, bao_f_eq, bao_Mphi, bao_v, Yang_G, Yang_F,
@@ -68,6 +68,14 @@ typedef enum pflb_family {
                                tau = max(nu_H, nu_L)/c_s^2 + 1/2. Periodic domains, FP32
                                storage, D2Q9 / D3Q19 + D3Q7; stepped by four passes
                                (phi, mu, u and p, collision) instead of the fused kernel */
+  PFLB_HAC_LIU2023 = 6      /* hybrid Allen-Cahn with lambda(x) = 1 within 3 xi of the
+                               interface and 0 elsewhere, from the log-transform predictor
+                               and reinitialisation (ceil(6 xi) Godunov steps of 1/2) of a
+                               signed distance; Liang2018's equilibria, forcing and updates,
+                               Sec. II C 5 (Eqs. Liu_G, Liu_F); gamma over the lambda = 0
+                               region. Periodic domains, FP32 storage, D2Q9 / D3Q19 + D3Q7;
+                               stepped by passes (phi*, reinitialisation, lambda and gamma,
+                               phi, collision) */
 } pflb_family;
 
 /* Population storage in device memory. Arithmetic is always FP32. The 16-bit

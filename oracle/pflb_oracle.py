@@ -650,12 +650,13 @@ def macroscopic(P, st, gamma=None):
         # lambda(x) of the reinitialised signed distance of phi*, gamma over the
         # lambda = 0 region, phi = phi* + (1 - lambda) R(phi*)/2 (as Reading R5,
         # with the local weight; Reading R22).
-        lam = liu_weight(P, liu_reinit(P, phi_star))
+        psi = liu_reinit(P, phi_star)
+        lam = liu_weight(P, psi)
         if gamma is None:
             gamma = liu_gamma(P, phi_star, lam)
         R = nonlocal_R(P, phi_star, gamma)
         phi = phi_star + 0.5 * (1.0 - lam) * R
-        m["gamma"], m["R"], m["lam"] = gamma, R, lam
+        m["gamma"], m["R"], m["lam"], m["psi"] = gamma, R, lam, psi
     else:
         phi = phi_star
     m["phi"] = phi

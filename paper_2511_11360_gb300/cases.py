@@ -15,12 +15,12 @@ import math
 
 import numpy as np
 
-FAKHARI2017, CHAI2018, HU2019, LIANG2014, LIANG2018, BAO2024 = 0, 1, 2, 3, 4, 5
+FAKHARI2017, CHAI2018, HU2019, LIANG2014, LIANG2018, BAO2024, LIU2023 = 0, 1, 2, 3, 4, 5, 6
 # Families of the fused step (every storage form, walls, the batched launch).
 FAMILIES = (FAKHARI2017, CHAI2018, HU2019, LIANG2014, LIANG2018)
 FAMILY_NAMES = {FAKHARI2017: "fakhari2017", CHAI2018: "chai2018",
                 HU2019: "hu2019", LIANG2014: "liang2014", LIANG2018: "liang2018",
-                BAO2024: "bao2024"}
+                BAO2024: "bao2024", LIU2023: "liu2023"}
 
 DEFAULT_SEED = 20251114
 

@@ -70,10 +70,10 @@ int validate(const pflb_params* p, char* msg, size_t n) {
   const long long qmax = p->dim == 2 ? 9 : 19;
   if (((N + 31) / 32) * 32 * qmax >= (1LL << 32))
     return snprintf(msg, n, "Q * cells must be < 2^32 (%lld cells max)", ((1LL << 32) - 1) / qmax / 32 * 32), PFLB_EINVAL;
-  if (p->family < 0 || p->family > 5) return snprintf(msg, n, "unknown family %d", p->family), PFLB_EINVAL;
-  if (p->family == PFLB_CH_BAO2024 && (p->storage != PFLB_FP32 || p->bc_y != 0 || p->lattice_f == 27 ||
+  if (p->family < 0 || p->family > 6) return snprintf(msg, n, "unknown family %d", p->family), PFLB_EINVAL;
+  if (p->family >= PFLB_CH_BAO2024 && (p->storage != PFLB_FP32 || p->bc_y != 0 || p->lattice_f == 27 ||
                                        p->collision != 0))
-    return snprintf(msg, n, "Bao2024 runs on periodic domains with FP32 storage and BGK on D2Q9 / D3Q19"),
+    return snprintf(msg, n, "Bao2024 and Liu2023 run on periodic domains with FP32 storage and BGK on D2Q9 / D3Q19"),
            PFLB_EINVAL;
   if (p->storage < 0 || p->storage > 2) return snprintf(msg, n, "unknown storage %d", p->storage), PFLB_EINVAL;
   if (p->bc_y < 0 || p->bc_y > 2) return snprintf(msg, n, "bc_y must be 0, 1 or 2"), PFLB_EINVAL;
@@ -158,6 +158,7 @@ DevParams derive(const pflb_params* p) {
   const double r = p->rho_H / p->rho_L;
   d.theta = (float)((r - 1.0) / (p->phi_H - p->phi_L * r));
   d.lks_itau = (float)(1.0 / (3.0 * (p->nu_H > p->nu_L ? p->nu_H : p->nu_L) + 0.5));
+  d.W_xi = (float)p->W;
   return d;
 }
 
@@ -168,7 +169,8 @@ void step_launch(int fam, int dim, int storage, const StepArgs& a, cudaStream_t 
     case 2: step_hu(dim, storage, a, s); break;
     case 3: step_liang2014(dim, storage, a, s); break;
     case 4: step_liang2018(dim, storage, a, s); break;
-    default: step_bao2024(dim, storage, a, s); break;
+    case 5: step_bao2024(dim, storage, a, s); break;
+    default: step_liu2023(dim, storage, a, s); break;
   }
 }
 
@@ -179,7 +181,8 @@ void init_launch(int fam, int dim, int storage, const InitArgs& a, cudaStream_t 
     case 2: init_hu(dim, storage, a, s); break;
     case 3: init_liang2014(dim, storage, a, s); break;
     case 4: init_liang2018(dim, storage, a, s); break;
-    default: init_bao2024(dim, storage, a, s); break;
+    case 5: init_bao2024(dim, storage, a, s); break;
+    default: init_liu2023(dim, storage, a, s); break;
   }
 }
 
@@ -262,6 +265,7 @@ int macro_pass(pflb_handle* h, float* phi, float* u, float* p) {
     gamma_sums(h->dim, h->storage, ga, h->stream);
     a.gamma_acc = acc;
   }
+  if (h->family == PFLB_HAC_LIU2023) a.gamma_acc = h->gamma_acc + 4;
   step_launch(h->family, h->dim, h->storage, a, h->stream);
   CU(h, cudaGetLastError());
   return PFLB_OK;
@@ -337,6 +341,7 @@ int pflb_create(const pflb_params* params, void* cuda_stream, pflb_handle** out)
   if (fam_phiu(h->family) && (rc = alloc((void**)&h->phiu, (size_t)h->dim * h->N * sizeof(float)))) return rc;
   if (h->family == PFLB_CH_BAO2024 && (rc = alloc((void**)&h->work, (size_t)(3 + h->dim) * h->N * sizeof(float))))
     return rc;
+  if (h->family == PFLB_HAC_LIU2023 && (rc = alloc((void**)&h->work, (size_t)6 * h->N * sizeof(float)))) return rc;
   if ((rc = alloc((void**)&h->obs, (size_t)(h->obs_cap + 1) * sizeof(DevObs)))) return rc;
   if ((rc = alloc((void**)&h->gamma_acc, 6 * sizeof(double)))) return rc;
   return PFLB_OK;
@@ -396,6 +401,7 @@ int pflb_step(pflb_handle* h, int64_t nsteps) {
       gamma_sums(h->dim, h->storage, ga, h->stream);
       a.gamma_acc = acc;
     }
+    if (h->family == PFLB_HAC_LIU2023) a.gamma_acc = h->gamma_acc + 2 * (h->step & 1);
     step_launch(h->family, h->dim, h->storage, a, h->stream);
     h->cur ^= 1;
     h->step += 1;
@@ -533,6 +539,13 @@ double pflb_bytes_per_update(const pflb_handle* h) {
     // macroscopic and collision passes, f read for u and p, u and p written
     // and read (field words of 4 bytes)
     b += 4.0 * (qg + 1) + 8.0 + 4.0 * h->QF + 8.0 + 4.0 * (h->dim + 1) + 4.0 * (3 + h->dim);
+  }
+  if (h->family == PFLB_HAC_LIU2023) {
+    // the passes: g read for phi*, phi* psi0 psi written; per reinitialisation
+    // step psi and psi0 read and psi written; lambda written, phi* read twice,
+    // lambda read twice, phi written and read (field words of 4 bytes)
+    const double nit = std::ceil(6.0 * h->prm.W);
+    b += 4.0 * qg + 12.0 + 12.0 * nit + 12.0 + 12.0 + 12.0;
   }
   if (fam_phiu(h->family)) b += 2.0 * h->dim * 4.0;  // phi*u read + write
   if (handle_nonlocal(h)) b += (double)qg * h->elem;         // g read by the gamma reduction

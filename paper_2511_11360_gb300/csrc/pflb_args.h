@@ -38,7 +38,7 @@ struct StepArgs {
   int chunk;              // cells per block along the marching axis
   long long N;
   double* gamma_next;     // nonlocal/hybrid: the next step's pair (zeroed by the batched pre-pass)
-  float* work;            // Bao2024: phi, mu, p, u fields ((3 + d) x N)
+  float* work;            // Bao2024: phi, mu, p, u fields ((3 + d) x N); Liu2023: 6 x N
 };
 
 struct InitArgs {
@@ -108,12 +108,14 @@ void step_hu(int dim, int storage, const StepArgs& a, cudaStream_t s);
 void step_liang2014(int dim, int storage, const StepArgs& a, cudaStream_t s);
 void step_liang2018(int dim, int storage, const StepArgs& a, cudaStream_t s);
 void step_bao2024(int dim, int storage, const StepArgs& a, cudaStream_t s);
+void step_liu2023(int dim, int storage, const StepArgs& a, cudaStream_t s);
 void init_fakhari(int dim, int storage, const InitArgs& a, cudaStream_t s);
 void init_chai(int dim, int storage, const InitArgs& a, cudaStream_t s);
 void init_hu(int dim, int storage, const InitArgs& a, cudaStream_t s);
 void init_liang2014(int dim, int storage, const InitArgs& a, cudaStream_t s);
 void init_liang2018(int dim, int storage, const InitArgs& a, cudaStream_t s);
 void init_bao2024(int dim, int storage, const InitArgs& a, cudaStream_t s);
+void init_liu2023(int dim, int storage, const InitArgs& a, cudaStream_t s);
 // pflb_aux.cu
 void gamma_sums(int dim, int storage, const GammaArgs& a, cudaStream_t s);
 void canon_copy(int dim, int storage, const CanonArgs& a, cudaStream_t s);

@@ -17,10 +17,13 @@ constexpr int FAM_HU = 2;
 constexpr int FAM_LIANG = 3;     // Liang2014 (Cahn-Hilliard)
 constexpr int FAM_LIANG18 = 4;   // Liang2018 (conservative Allen-Cahn, conservative NS form)
 constexpr int FAM_BAO = 5;       // Bao2024 (Cahn-Hilliard, singular mobility, multi-pass step)
+constexpr int FAM_LIU = 6;       // Liu2023 (hybrid AC, lambda(x) from a signed distance, multi-pass step)
 
 // Families that keep phi*u of the previous step for d_t(phi u) (Sec. III B)
 // and use the pressure-based hydrodynamic equilibrium (Eq. liang2_feq).
-__host__ __device__ constexpr bool fam_phiu(int fam) { return fam == FAM_LIANG || fam == FAM_LIANG18; }
+__host__ __device__ constexpr bool fam_phiu(int fam) {
+  return fam == FAM_LIANG || fam == FAM_LIANG18 || fam == FAM_LIU;
+}
 
 // ---------------------------------------------------------------------------
 // Lattices (c_s^2 = 1/3 for all three, Sec. III and Sec. IV), in the
@@ -185,6 +188,7 @@ struct DevParams {
   float mrt_sb, mrt_sh;     // MRT rates: trace of the second moments, orders >= 3
   float theta;              // Bao2024: quasi-incompressible theta (Eq. quasi_incomp_system)
   float lks_itau;           // Bao2024: 1 / tau of the lattice kinetic scheme (constant)
+  float W_xi;               // interface thickness xi (Liu2023: d_min = 3 xi, predictor scale)
 };
 
 // Observables accumulated by one pass (one slot of the per-step ring).

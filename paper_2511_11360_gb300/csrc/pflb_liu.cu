@@ -1,0 +1,267 @@
+// Liu2023 (Sec. II C 5): hybrid Allen-Cahn whose weight lambda(x) is 1 within
+// d_min = 3 xi of the interface and 0 elsewhere, with Liang2018's equilibria,
+// forcing and updates (Eqs. Liu_G, Liu_F); Reading R22 for the reconstruction.
+//
+// lambda needs a signed distance of the whole field before any collision, so
+// the step runs as grid-stride passes over the domain (periodic, FP32, same
+// population layout and AA / push streaming as the fused step):
+//   1. phi* = sum g; predictor psi0 = -(xi/4) ln((phi_H - phi_L)/(phi* - phi_L) - 1)
+//      (phi* clamped to [phi_L + 0.01, phi_H - 0.01])
+//   2. ceil(2 d_min) pseudo-time steps (dt' = 1/2) of the reinitialisation
+//      equation d psi/dt' + S(psi0)(|grad psi| - 1) = 0, first-order Godunov
+//      upwinding, S(psi0) = psi0 / sqrt(psi0^2 + 1)
+//   3. lambda = [|psi| < d_min]; the (1 - lambda)-weighted integrals of Eq.
+//      (lagrange_multiplier) in FP64
+//   4. phi = phi* + (1 - lambda) R(phi*) / 2
+//   5. collision (the Liang2018 update of the fused step with Eq. Liu_G's
+//      mix), streaming, observables.
+// Work fields (N floats each): phi*, psi0, psi_a, psi_b, lambda, phi.
+#include "pflb_init.cuh"
+
+namespace pflb {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <int DIM>
+struct LiuGeo {
+  int nx, ny, nz;
+  __device__ __forceinline__ void coords(long long c, int& x, int& y, int& z) const {
+    x = (int)(c % nx);
+    y = (int)((c / nx) % ny);
+    z = DIM == 3 ? (int)(c / ((long long)nx * ny)) : 0;
+  }
+  __device__ __forceinline__ unsigned nb(int x, int y, int z, int ex, int ey, int ez) const {
+    int xn = x + ex, yn = y + ey, zn = z + ez;
+    xn = xn < 0 ? xn + nx : (xn >= nx ? xn - nx : xn);
+    yn = yn < 0 ? yn + ny : (yn >= ny ? yn - ny : yn);
+    if (DIM == 3) zn = zn < 0 ? zn + nz : (zn >= nz ? zn - nz : zn);
+    return (unsigned)(xn + nx * (yn + (DIM == 3 ? ny * zn : 0)));
+  }
+};
+
+struct LiuWork {
+  float *phis, *psi0, *psia, *psib, *lam, *phi;
+};
+__host__ __device__ inline LiuWork liu_work(float* w, long long N) {
+  return LiuWork{w, w + N, w + 2 * N, w + 3 * N, w + 4 * N, w + 5 * N};
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) liu_predict_kernel(const StepArgs a) {
+  using LG = typename Lattices<DIM>::G;
+  constexpr bool SKIP0 = DIM == 3;   // D3Q7 rest population of the Allen-Cahn families is zero
+  const DevParams& P = a.p;
+  const LiuWork W = liu_work(a.work, a.N);
+  const float* g = static_cast<const float*>(a.g_src);
+  const float lo = P.phiL + 0.01f, hi = P.phiH - 0.01f, dphi = P.phiH - P.phiL;
+  for (long long c = blockIdx.x * (long long)kThreads + threadIdx.x; c < a.N; c += (long long)gridDim.x * kThreads) {
+    float v[LG::Q];
+#pragma unroll
+    for (int q = 0; q < LG::Q; ++q) v[q] = (SKIP0 && q == 0) ? 0.0f : g[pop_ix<LG>(q, (unsigned)c)];
+    const float ps = phi_star<LG, SKIP0>(v);
+    W.phis[c] = ps;
+    const float pc = fminf(fmaxf(ps, lo), hi);
+    const float psi = -0.25f * P.W_xi * logf(dphi / (pc - P.phiL) - 1.0f);
+    W.psi0[c] = psi;
+    W.psia[c] = psi;
+  }
+}
+
+// One Godunov step of the reinitialisation equation (Reading R22).
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) liu_reinit_kernel(const float* psi_in, float* psi_out, const float* psi0,
+                                                              long long N, LiuGeo<DIM> G) {
+  for (long long c = blockIdx.x * (long long)kThreads + threadIdx.x; c < N; c += (long long)gridDim.x * kThreads) {
+    int x, y, z;
+    G.coords(c, x, y, z);
+    const float p = psi_in[c], p0 = psi0[c];
+    const float S = p0 * rsqrtf(p0 * p0 + 1.0f);
+    float g2p = 0.0f, g2m = 0.0f;
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax) {
+      const float pm = psi_in[G.nb(x, y, z, ax == 0 ? -1 : 0, ax == 1 ? -1 : 0, ax == 2 ? -1 : 0)];
+      const float pp = psi_in[G.nb(x, y, z, ax == 0 ? 1 : 0, ax == 1 ? 1 : 0, ax == 2 ? 1 : 0)];
+      const float dm = p - pm, dp = pp - p;
+      const float a1 = fmaxf(dm, 0.0f), b1 = fminf(dp, 0.0f);
+      const float a2 = fminf(dm, 0.0f), b2 = fmaxf(dp, 0.0f);
+      g2p += fmaxf(a1 * a1, b1 * b1);
+      g2m += fmaxf(a2 * a2, b2 * b2);
+    }
+    const float grad = sqrtf(S > 0.0f ? g2p : g2m);
+    psi_out[c] = p - 0.5f * S * (grad - 1.0f);
+  }
+}
+
+// lambda and the (1 - lambda)-weighted integrals I1, I2 (FP64 per block, one
+// atomic per block into acc).
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) liu_gamma_kernel(const StepArgs a, const float* psi, double* acc) {
+  const DevParams& P = a.p;
+  const LiuWork W = liu_work(a.work, a.N);
+  const float dmin = 3.0f * P.W_xi;
+  double s1 = 0.0, s2 = 0.0;
+  for (long long c = blockIdx.x * (long long)kThreads + threadIdx.x; c < a.N; c += (long long)gridDim.x * kThreads) {
+    const float lam = fabsf(psi[c]) < dmin ? 1.0f : 0.0f;
+    W.lam[c] = lam;
+    if (lam == 0.0f) {
+      const float ps = W.phis[c];
+      s1 += (double)(P.four_beta_over_kappa * (ps - P.phiH) * (ps - P.phiL) * (ps - P.phi0));
+      s2 += (double)((P.phiH - ps) * (ps - P.phiL));
+    }
+  }
+  s1 = warp_sum(s1);
+  s2 = warp_sum(s2);
+  __shared__ double sh[2 * (kThreads / 32)];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    sh[2 * warp] = s1;
+    sh[2 * warp + 1] = s2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t1 = 0.0, t2 = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) {
+      t1 += sh[2 * w];
+      t2 += sh[2 * w + 1];
+    }
+    atomicAdd(acc, t1);
+    atomicAdd(acc + 1, t2);
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) liu_phi_kernel(const StepArgs a, const double* acc) {
+  const DevParams& P = a.p;
+  const LiuWork W = liu_work(a.work, a.N);
+  const double I2 = acc[1];
+  const float gamma = I2 != 0.0 ? (float)(acc[0] / I2) : 0.0f;
+  for (long long c = blockIdx.x * (long long)kThreads + threadIdx.x; c < a.N; c += (long long)gridDim.x * kThreads) {
+    const float ps = W.phis[c];
+    W.phi[c] = ps + 0.5f * (1.0f - W.lam[c]) * nonlocal_R<FAM_LIU>(P, ps, gamma);
+  }
+}
+
+// Collision (Liang2018 with Eq. Liu_G's mix), streaming and observables.
+template <int DIM>
+__global__ void __launch_bounds__(kThreads) liu_collide_kernel(const StepArgs a, const double* acc, LiuGeo<DIM> G) {
+  using LG = typename Lattices<DIM>::G;
+  using LF = typename Lattices<DIM>::F;
+  using LS = typename Lattices<DIM>::S;
+  constexpr bool SKIP0 = DIM == 3;
+  const DevParams& P = a.p;
+  const LiuWork W = liu_work(a.work, a.N);
+  const float* gs = static_cast<const float*>(a.g_src);
+  float* gd = static_cast<float*>(a.g_dst);
+  float* fb = static_cast<float*>(a.f);
+  const double I2 = acc[1];
+  const float gamma = I2 != 0.0 ? (float)(acc[0] / I2) : 0.0f;
+  __shared__ double s_red[(kThreads / 32) * 10];
+  if (a.obs_zero != nullptr && blockIdx.x == 0 && threadIdx.x == 0) obs_zero_slot(a.obs_zero);
+  ObsPartial obs;
+  obs_init(obs);
+  for (long long c = blockIdx.x * (long long)kThreads + threadIdx.x; c < a.N; c += (long long)gridDim.x * kThreads) {
+    int x, y, z;
+    G.coords(c, x, y, z);
+    float nb[LS::Q];
+#pragma unroll
+    for (int q = 0; q < LS::Q; ++q) nb[q] = W.phi[G.nb(x, y, z, LS::ex(q), LS::ey(q), LS::ez(q))];
+    const float pc = nb[0];
+    float gp[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) gp[k] = Sym<LS>::grad(nb, k);
+    const float lp = Sym<LS>::lap(nb, pc);
+    float g[LG::Q], f[LF::Q], phiu[DIM];
+#pragma unroll
+    for (int q = 0; q < LG::Q; ++q) g[q] = (SKIP0 && q == 0) ? 0.0f : gs[pop_ix<LG>(q, (unsigned)c)];
+#pragma unroll
+    for (int q = 0; q < LF::Q; ++q)
+      f[q] = a.parity == 0 ? fb[pop_ix<LF>(q, (unsigned)c)]
+                           : fb[pop_ix<LF>(LF::opp(q), G.nb(x, y, z, -LF::ex(q), -LF::ey(q), -LF::ez(q)))];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) phiu[k] = a.phiu[k * a.N + c];
+    float u[DIM], rho, p;
+    const float lam = W.lam[c];
+    Cell<FAM_LIU, DIM>::collide(P, g, f, pc, W.phis[c], gp, lp, 0.0f, 0.0f, phiu, gamma, u, rho, p, lam);
+    {
+      comp_add(obs.s_hi, obs.s_lo, pc);
+      const float fr = (pc - P.phiL) * P.inv_dphi;
+      float usq = 0.0f;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) usq += u[k] * u[k];
+      obs.vs += fr;
+      obs.ke += 0.5f * rho * usq;
+      obs.cx += (float)x * fr;
+      obs.cy += (float)y * fr;
+      if (DIM == 3) obs.cz += (float)z * fr;
+      obs.count += (pc > P.phi0) ? 1u : 0u;
+      obs.mx = fmaxf(obs.mx, pc);
+      obs.mn = fminf(obs.mn, pc);
+    }
+    if (a.macro) {
+      a.out_phi[c] = pc;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) a.out_u[k * a.N + c] = u[k];
+      a.out_p[c] = p;
+      continue;
+    }
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) a.phiu[k * a.N + c] = phiu[k];
+#pragma unroll
+    for (int q = 0; q < LG::Q; ++q)
+      if (!(SKIP0 && q == 0)) gd[pop_ix<LG>(q, G.nb(x, y, z, LG::ex(q), LG::ey(q), LG::ez(q)))] = g[q];
+#pragma unroll
+    for (int q = 0; q < LF::Q; ++q) {
+      if (a.parity == 0) fb[pop_ix<LF>(LF::opp(q), (unsigned)c)] = f[q];
+      else fb[pop_ix<LF>(q, G.nb(x, y, z, LF::ex(q), LF::ey(q), LF::ez(q)))] = f[q];
+    }
+  }
+  if (obs.mn <= obs.mx) {
+    const float r1 = P.rhoL + P.drho_dphi * (obs.mn - P.phiL), r2 = P.rhoL + P.drho_dphi * (obs.mx - P.phiL);
+    if (!(isfinite(obs.s_hi) && isfinite(obs.ke) && r1 > 0.0f && r2 > 0.0f)) obs.bad = 1u;
+  }
+  obs_block_commit(obs, a.obs_slot, s_red);
+}
+
+int grid_for(long long N) {
+  const long long want = (N + kThreads - 1) / kThreads;
+  const long long cap = 8LL * 152;
+  return (int)(want < cap ? want : cap);
+}
+
+template <int DIM>
+void liu_step_dim(const StepArgs& a, cudaStream_t s) {
+  LiuGeo<DIM> G{a.p.nx, a.p.ny, DIM == 3 ? a.p.nz : 1};
+  const int grid = grid_for(a.N);
+  const LiuWork W = liu_work(a.work, a.N);
+  liu_predict_kernel<DIM><<<grid, kThreads, 0, s>>>(a);
+  const int nit = (int)ceilf(2.0f * 3.0f * a.p.W_xi);
+  const float* in = W.psia;
+  float* out = W.psib;
+  for (int it = 0; it < nit; ++it) {
+    liu_reinit_kernel<DIM><<<grid, kThreads, 0, s>>>(in, out, W.psi0, a.N, G);
+    const float* t = out;
+    out = const_cast<float*>(in);
+    in = t;
+  }
+  // gamma_acc holds this step's (I1, I2) pair, zeroed here
+  double* acc = const_cast<double*>(a.gamma_acc);
+  cudaMemsetAsync(acc, 0, 2 * sizeof(double), s);
+  liu_gamma_kernel<DIM><<<grid, kThreads, 0, s>>>(a, in, acc);
+  liu_phi_kernel<DIM><<<grid, kThreads, 0, s>>>(a, acc);
+  liu_collide_kernel<DIM><<<grid, kThreads, 0, s>>>(a, acc, G);
+}
+
+}  // namespace
+
+void step_liu2023(int dim, int storage, const StepArgs& a, cudaStream_t s) {
+  (void)storage;   // FP32 only (validated by the API)
+  if (dim == 2) liu_step_dim<2>(a, s);
+  else liu_step_dim<3>(a, s);
+}
+
+void init_liu2023(int dim, int storage, const InitArgs& a, cudaStream_t s) {
+  init_dispatch<FAM_LIU>(dim, storage, a, s);
+}
+
+}  // namespace pflb

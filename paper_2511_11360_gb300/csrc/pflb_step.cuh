@@ -100,10 +100,13 @@ struct Cell {
   // Size of the MRT work array: 27 on D3Q27 (the collision has an MRT form), 1 otherwise.
   static constexpr int MRT_Q = (QF == 27) ? 27 : 1;
 
+  // Liu2023 is Liang2018 with the local weight lamx of its G (Eq. Liu_G).
+  static constexpr bool L18 = (FAM == FAM_LIANG18 || FAM == FAM_LIU);
+
   __device__ __forceinline__ static void collide(
       const DevParams& P, float (&g)[QG], float (&f)[QF], float phi, float phis,
       const float (&gp)[DIM], float lp, float mu_in, float lmu, float (&phiu)[DIM],
-      float gamma, float (&u)[DIM], float& rho, float& p) {
+      float gamma, float (&u)[DIM], float& rho, float& p, float lamx = 1.0f) {
     constexpr float cs2 = 1.0f / 3.0f;
     rho = P.rhoL + P.drho_dphi * (phi - P.phiL);
     const float nu = viscosity(P, phi, rho);
@@ -126,7 +129,7 @@ struct Cell {
     const float A = P.lundA;
     float F[DIM];
 
-    if constexpr (FAM == FAM_LIANG18) {
+    if constexpr (L18) {
       // Liang2018: rho u = sum e f + F/2 with F = F_s + F_b (Eq.
       // liang_velocity_update); the linear forcing A rho u is solved for.
       const float den = inv_rho / (1.0f - 0.5f * A);
@@ -219,7 +222,7 @@ struct Cell {
       geq[0] = phi - Sym<LG>::moving(geq);   // = phi + (w_0 - 1) eta mu
     } else {
       float flux[DIM];
-      constexpr bool has_cons = (FAM == FAM_FAKHARI || FAM == FAM_HU || FAM == FAM_LIANG18);
+      constexpr bool has_cons = (FAM == FAM_FAKHARI || FAM == FAM_HU || L18);
       if (has_cons) {
         // Conservative counter term, Eq. (fakhari_G_modified), with the
         // normal regularised as grad phi / sqrt(|grad phi|^2 + eps^2) (R6).
@@ -232,7 +235,7 @@ struct Cell {
       }
       // Liang2018: backward-Euler d_t(phi u) (Sec. III B) for Eq. (liang_G_final).
       float dpu[DIM];
-      if constexpr (FAM == FAM_LIANG18) {
+      if constexpr (L18) {
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
           const float pu = phi * u[k];
@@ -245,6 +248,10 @@ struct Cell {
         Rw = nonlocal_R<FAM>(P, phis, gamma);
         if constexpr (FAM == FAM_HU) { lam = P.lambda; Rw *= (1.0f - lam); }
       }
+      if constexpr (FAM == FAM_LIU) {
+        lam = lamx;
+        Rw = (1.0f - lam) * nonlocal_R<FAM>(P, phis, gamma);
+      }
       geq[0] = 0.0f;
       G[0] = 0.0f;
 #pragma unroll
@@ -255,7 +262,7 @@ struct Cell {
           if (ecomp<LG>(q, k) != 0) {
             eu += (float)ecomp<LG>(q, k) * u[k];
             if constexpr (has_cons) ef += (float)ecomp<LG>(q, k) * flux[k];
-            if constexpr (FAM == FAM_LIANG18) ef += (float)ecomp<LG>(q, k) * (3.0f * dpu[k]);
+            if constexpr (L18) ef += (float)ecomp<LG>(q, k) * (3.0f * dpu[k]);
           }
         if constexpr (FAM == FAM_FAKHARI)
           geq[q] = wmul<LG>(q, phi * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * usq));  // Eq. (fakhari_geq)
@@ -263,11 +270,11 @@ struct Cell {
           geq[q] = wmul<LG>(q, phi * (1.0f + 3.0f * eu));                   // Eqs. (Chai_geq), (liang_geq)
         if constexpr (FAM == FAM_FAKHARI || FAM == FAM_LIANG18) G[q] = wmul<LG>(q, ef);  // Eq. (liang_G_final)
         else if constexpr (FAM == FAM_CHAI) G[q] = wmul<LG>(q, Rw);
-        else G[q] = wmul<LG>(q, lam * ef + Rw);                                        // Eq. (Hu_G)
+        else G[q] = wmul<LG>(q, lam * ef + Rw);                          // Eqs. (Hu_G), (Liu_G)
       }
       if constexpr (REST) {
         geq[0] = phi - Sym<LG>::moving(geq);
-        if constexpr (FAM == FAM_CHAI || FAM == FAM_HU) G[0] = wmul<LG>(0, Rw);
+        if constexpr (FAM == FAM_CHAI || FAM == FAM_HU || FAM == FAM_LIU) G[0] = wmul<LG>(0, Rw);
       }
     }
 #pragma unroll

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libpflb.so")
 
 PFLB_OK, PFLB_EINVAL, PFLB_ENOMEM, PFLB_ECUDA, PFLB_EUNSTABLE, PFLB_ETIMEOUT = 0, -1, -2, -3, -4, -5
-FAKHARI2017, CHAI2018, HU2019, LIANG2014, LIANG2018, BAO2024 = 0, 1, 2, 3, 4, 5
+FAKHARI2017, CHAI2018, HU2019, LIANG2014, LIANG2018, BAO2024, LIU2023 = 0, 1, 2, 3, 4, 5, 6
 FP32, FP16_DEV, BF16_DEV = 0, 1, 2
 STORAGE = {"fp32": FP32, "fp16": FP16_DEV, "bf16": BF16_DEV}
 
