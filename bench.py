@@ -430,7 +430,7 @@ def main():
             # The other families on the same workload and storage (the paper's
             # Table III compares the families' cost on one 3D case).
             fams = {}
-            for fam in (C.CHAI2018, C.HU2019, C.LIANG2014, C.LIANG2018, C.BAO2024):
+            for fam in (C.CHAI2018, C.HU2019, C.LIANG2014, C.LIANG2018, C.BAO2024, C.LIU2023):
                 s3 = pflb.Sim(dict(P, family=fam, storage=storage, obs_capacity=4),
                               stream=torch.cuda.current_stream())
                 s3.init(phi, u)
