@@ -52,8 +52,12 @@ int default_chunk(const pflb_handle* h) {
   const long long tiles = (long long)((NA + ta - 1) / ta) * ((NB + tb - 1) / tb);
   const long long target = 8LL * num_sms();
   long long c = (tiles * NC + target - 1) / target;
+  // Longer marches amortise the prologue (two planes of phi) and keep each
+  // block's reads on fewer DRAM pages; 128 planes measured best at 512^3
+  // (FP32 24.9 vs 24.8 GLUPS at 64, FP16 31.3 vs 30.7), with at least ~8
+  // blocks per SM still in the grid.
   if (c < 4) c = 4;
-  if (c > 64) c = 64;
+  if (c > 128) c = 128;
   if (c > NC) c = NC;
   return (int)c;
 }
