@@ -13,38 +13,21 @@
 //      observables of the state
 //   4. collision of g and f with the stencils of phi, mu, M(phi), u, p;
 //      streaming.
-// The work buffer holds (3 + d) fields: phi, mu, p, u_x, u_y[, u_z].
+// The work buffer holds (3 + d) fields: phi, mu, p, u_x, u_y[, u_z]. Every
+// pass walks the domain as (x, y) tiles marching in z (pflb_pass.cuh).
 #include "pflb_init.cuh"
+#include "pflb_pass.cuh"
 
 namespace pflb {
 namespace {
 
-constexpr int kThreads = 256;
-
-template <int DIM>
-struct BaoGeo {
-  int nx, ny, nz;
-  __device__ __forceinline__ void coords(long long c, int& x, int& y, int& z) const {
-    x = (int)(c % nx);
-    y = (int)((c / nx) % ny);
-    z = DIM == 3 ? (int)(c / ((long long)nx * ny)) : 0;
-  }
-  // Cell index of (x, y, z) + e (periodic).
-  __device__ __forceinline__ unsigned nb(int x, int y, int z, int ex, int ey, int ez) const {
-    int xn = x + ex, yn = y + ey, zn = z + ez;
-    xn = xn < 0 ? xn + nx : (xn >= nx ? xn - nx : xn);
-    yn = yn < 0 ? yn + ny : (yn >= ny ? yn - ny : yn);
-    if (DIM == 3) zn = zn < 0 ? zn + nz : (zn >= nz ? zn - nz : zn);
-    return (unsigned)(xn + nx * (yn + (DIM == 3 ? ny * zn : 0)));
-  }
-};
+constexpr int kThreads = kPassThreads;
 
 // Field values at the stencil neighbours x + e_q of the stencil lattice.
 template <int DIM, typename LS>
-__device__ __forceinline__ void gather(const float* fld, const BaoGeo<DIM>& G, int x, int y, int z,
-                                       float (&v)[LS::Q]) {
+__device__ __forceinline__ void gather(const float* fld, const PassCell& cl, float (&v)[LS::Q]) {
 #pragma unroll
-  for (int q = 0; q < LS::Q; ++q) v[q] = fld[G.nb(x, y, z, LS::ex(q), LS::ey(q), LS::ez(q))];
+  for (int q = 0; q < LS::Q; ++q) v[q] = fld[cl.nb(LS::ex(q), LS::ey(q), LS::ez(q))];
 }
 
 // Singular mobility M(phi), Eq. (bao_singular_mobility); M_0 = P.M.
@@ -53,42 +36,40 @@ __device__ __forceinline__ float bao_M(const DevParams& P, float phi) {
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(kThreads) bao_phi_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(kThreads) bao_phi_kernel(const StepArgs a, PassGeo<DIM> G) {
   using LG = typename Lattices<DIM>::G;
   const float* g = static_cast<const float*>(a.g_src);
   float* phi = a.work;
-  for (long long c = blockIdx.x * (long long)kThreads + threadIdx.x; c < a.N; c += (long long)gridDim.x * kThreads) {
+  pass_walk<DIM>(G, [&](const PassCell& cl) {
     float v[LG::Q];
 #pragma unroll
-    for (int q = 0; q < LG::Q; ++q) v[q] = g[pop_ix<LG>(q, (unsigned)c)];
-    phi[c] = v[0] + Sym<LG>::moving(v);   // Eq. (fakhari_phi_update)
-  }
+    for (int q = 0; q < LG::Q; ++q) v[q] = g[pop_ix<LG>(q, cl.c)];
+    phi[cl.c] = v[0] + Sym<LG>::moving(v);   // Eq. (fakhari_phi_update)
+  });
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(kThreads) bao_mu_kernel(const StepArgs a, BaoGeo<DIM> G) {
+__global__ void __launch_bounds__(kThreads) bao_mu_kernel(const StepArgs a, PassGeo<DIM> G) {
   using LS = typename Lattices<DIM>::S;
   const DevParams& P = a.p;
   const float* phi = a.work;
   float* mu = a.work + a.N;
-  for (long long c = blockIdx.x * (long long)kThreads + threadIdx.x; c < a.N; c += (long long)gridDim.x * kThreads) {
-    int x, y, z;
-    G.coords(c, x, y, z);
+  pass_walk<DIM>(G, [&](const PassCell& cl) {
     float v[LS::Q];
-    gather<DIM, LS>(phi, G, x, y, z, v);
+    gather<DIM, LS>(phi, cl, v);
     const float pc = v[0];
-    mu[c] = P.beta4 * (pc - P.phiH) * (pc - P.phiL) * (pc - P.phi0) - P.kappa * Sym<LS>::lap(v, pc);  // Eq. (chemical_potential)
-  }
+    mu[cl.c] = P.beta4 * (pc - P.phiH) * (pc - P.phiL) * (pc - P.phi0) - P.kappa * Sym<LS>::lap(v, pc);  // Eq. (chemical_potential)
+  });
 }
 
 // grad mu, lap mu and div(M grad mu) = M lap mu + grad M . grad mu (Reading R21)
 template <int DIM>
-__device__ __forceinline__ void bao_flux(const DevParams& P, const float* phi, const float* mu, const BaoGeo<DIM>& G,
-                                         int x, int y, int z, float phic, float (&gmu)[DIM], float& divJ) {
+__device__ __forceinline__ void bao_flux(const DevParams& P, const float* phi, const float* mu, const PassCell& cl,
+                                         float phic, float (&gmu)[DIM], float& divJ) {
   using LS = typename Lattices<DIM>::S;
   float vm[LS::Q], vp[LS::Q];
-  gather<DIM, LS>(mu, G, x, y, z, vm);
-  gather<DIM, LS>(phi, G, x, y, z, vp);
+  gather<DIM, LS>(mu, cl, vm);
+  gather<DIM, LS>(phi, cl, vp);
   float vM[LS::Q];
 #pragma unroll
   for (int q = 0; q < LS::Q; ++q) vM[q] = bao_M(P, vp[q]);
@@ -104,7 +85,7 @@ __device__ __forceinline__ void bao_flux(const DevParams& P, const float* phi, c
 
 // Pass 3: u, p and the observables of the state.
 template <int DIM>
-__global__ void __launch_bounds__(kThreads) bao_macro_kernel(const StepArgs a, BaoGeo<DIM> G) {
+__global__ void __launch_bounds__(kThreads) bao_macro_kernel(const StepArgs a, PassGeo<DIM> G) {
   using LF = typename Lattices<DIM>::F;
   using LS = typename Lattices<DIM>::S;
   constexpr float cs2 = 1.0f / 3.0f;
@@ -115,24 +96,26 @@ __global__ void __launch_bounds__(kThreads) bao_macro_kernel(const StepArgs a, B
   float* uf = a.work + 3 * a.N;
   const float* fb = static_cast<const float*>(a.f);
   __shared__ double s_red[(kThreads / 32) * 10];
-  if (a.obs_zero != nullptr && blockIdx.x == 0 && threadIdx.x == 0) obs_zero_slot(a.obs_zero);
+  if (a.obs_zero != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&
+      threadIdx.y == 0)
+    obs_zero_slot(a.obs_zero);
   ObsPartial obs;
   obs_init(obs);
   const float theta = P.theta;   // quasi-incompressible theta, Eq. (quasi_incomp_system)
-  for (long long c = blockIdx.x * (long long)kThreads + threadIdx.x; c < a.N; c += (long long)gridDim.x * kThreads) {
-    int x, y, z;
-    G.coords(c, x, y, z);
+  pass_walk<DIM>(G, [&](const PassCell& cl) {
+    const unsigned c = cl.c;
+    const int x = cl.x, y = cl.y, z = cl.z;
     // incoming f (AA): even steps slot q of the own cell, odd steps slot opp(q) of x - e_q
     float f[LF::Q];
 #pragma unroll
     for (int q = 0; q < LF::Q; ++q)
       f[q] = a.parity == 0 ? fb[pop_ix<LF>(q, (unsigned)c)]
-                           : fb[pop_ix<LF>(LF::opp(q), G.nb(x, y, z, -LF::ex(q), -LF::ey(q), -LF::ez(q)))];
+                           : fb[pop_ix<LF>(LF::opp(q), cl.nb(-LF::ex(q), -LF::ey(q), -LF::ez(q)))];
     float vp[LS::Q];
-    gather<DIM, LS>(phi, G, x, y, z, vp);
+    gather<DIM, LS>(phi, cl, vp);
     const float pc = vp[0];
     float gp[DIM], gmu[DIM], divJ;
-    bao_flux<DIM>(P, phi, mu, G, x, y, z, pc, gmu, divJ);
+    bao_flux<DIM>(P, phi, mu, cl, pc, gmu, divJ);
     const float rho = P.rhoL + P.drho_dphi * (pc - P.phiL);
     const float muc = mu[c];
     float u[DIM], Fs[DIM], Fb[DIM];
@@ -170,7 +153,7 @@ __global__ void __launch_bounds__(kThreads) bao_macro_kernel(const StepArgs a, B
     obs.count += (pc > P.phi0) ? 1u : 0u;
     obs.mx = fmaxf(obs.mx, pc);
     obs.mn = fminf(obs.mn, pc);
-  }
+  });
   if (obs.mn <= obs.mx) {
     const float r1 = P.rhoL + P.drho_dphi * (obs.mn - P.phiL), r2 = P.rhoL + P.drho_dphi * (obs.mx - P.phiL);
     if (!(isfinite(obs.s_hi) && isfinite(obs.ke) && r1 > 0.0f && r2 > 0.0f)) obs.bad = 1u;
@@ -189,7 +172,7 @@ __device__ __forceinline__ float gam_w(int q, const float (&u)[DIM], float usq) 
 
 // Pass 4: collision and streaming.
 template <int DIM>
-__global__ void __launch_bounds__(kThreads) bao_collide_kernel(const StepArgs a, BaoGeo<DIM> G) {
+__global__ void __launch_bounds__(kThreads) bao_collide_kernel(const StepArgs a, PassGeo<DIM> G) {
   using LG = typename Lattices<DIM>::G;
   using LF = typename Lattices<DIM>::F;
   using LS = typename Lattices<DIM>::S;
@@ -205,15 +188,14 @@ __global__ void __launch_bounds__(kThreads) bao_collide_kernel(const StepArgs a,
   const float theta = P.theta;
   const float itp = P.inv_tau_phi, swp = P.src_w_phi;   // constant tau_phi (Reading R21)
   const float itau = P.lks_itau, fwt = 1.0f - 0.5f * P.lks_itau;
-  for (long long c = blockIdx.x * (long long)kThreads + threadIdx.x; c < a.N; c += (long long)gridDim.x * kThreads) {
-    int x, y, z;
-    G.coords(c, x, y, z);
+  pass_walk<DIM>(G, [&](const PassCell& cl) {
+    const unsigned c = cl.c;
     float vp[LS::Q], vpr[LS::Q];
-    gather<DIM, LS>(phi, G, x, y, z, vp);
-    gather<DIM, LS>(pf, G, x, y, z, vpr);
+    gather<DIM, LS>(phi, cl, vp);
+    gather<DIM, LS>(pf, cl, vpr);
     const float pc = vp[0], p = vpr[0], muc = mu[c];
     float gmu[DIM], divJ;
-    bao_flux<DIM>(P, phi, mu, G, x, y, z, pc, gmu, divJ);
+    bao_flux<DIM>(P, phi, mu, cl, pc, gmu, divJ);
     const float rho = P.rhoL + P.drho_dphi * (pc - P.phiL);
     const float nu = viscosity(P, pc, rho);
     const float A_lks = (1.0f / itp) - 0.5f - bao_M(P, pc) * 3.0f / P.eta;   // Eq. (bao_Mphi)
@@ -234,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) bao_collide_kernel(const StepArgs a,
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
       float vu[LS::Q];
-      gather<DIM, LS>(uf + k * a.N, G, x, y, z, vu);
+      gather<DIM, LS>(uf + k * a.N, cl, vu);
 #pragma unroll
       for (int i = 0; i < DIM; ++i) du[k][i] = Sym<LS>::grad(vu, i);
     }
@@ -248,7 +230,7 @@ __global__ void __launch_bounds__(kThreads) bao_collide_kernel(const StepArgs a,
     // ---- phase field: Eqs. (bao_g_eq), (Yang_G)
     float g[LG::Q], geq[LG::Q], Gs[LG::Q];
 #pragma unroll
-    for (int q = 0; q < LG::Q; ++q) g[q] = gs[pop_ix<LG>(q, (unsigned)c)];
+    for (int q = 0; q < LG::Q; ++q) g[q] = gs[pop_ix<LG>(q, c)];
     float V[DIM], uV = 0.0f;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
@@ -281,7 +263,7 @@ __global__ void __launch_bounds__(kThreads) bao_collide_kernel(const StepArgs a,
 #pragma unroll
     for (int q = 0; q < LF::Q; ++q)
       f[q] = a.parity == 0 ? fb[pop_ix<LF>(q, (unsigned)c)]
-                           : fb[pop_ix<LF>(LF::opp(q), G.nb(x, y, z, -LF::ex(q), -LF::ey(q), -LF::ez(q)))];
+                           : fb[pop_ix<LF>(LF::opp(q), cl.nb(-LF::ex(q), -LF::ey(q), -LF::ez(q)))];
     float uF = 0.0f, ugr = 0.0f;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
@@ -306,33 +288,31 @@ __global__ void __launch_bounds__(kThreads) bao_collide_kernel(const StepArgs a,
     }
     // ---- streaming: g pushed to x + e into the other array; f AA
 #pragma unroll
-    for (int q = 0; q < LG::Q; ++q) gd[pop_ix<LG>(q, G.nb(x, y, z, LG::ex(q), LG::ey(q), LG::ez(q)))] = g[q];
+    for (int q = 0; q < LG::Q; ++q) gd[pop_ix<LG>(q, cl.nb(LG::ex(q), LG::ey(q), LG::ez(q)))] = g[q];
 #pragma unroll
     for (int q = 0; q < LF::Q; ++q) {
-      if (a.parity == 0) fb[pop_ix<LF>(LF::opp(q), (unsigned)c)] = f[q];
-      else fb[pop_ix<LF>(q, G.nb(x, y, z, LF::ex(q), LF::ey(q), LF::ez(q)))] = f[q];
+      if (a.parity == 0) fb[pop_ix<LF>(LF::opp(q), c)] = f[q];
+      else fb[pop_ix<LF>(q, cl.nb(LF::ex(q), LF::ey(q), LF::ez(q)))] = f[q];
     }
-  }
+  });
 }
 
 // Initial state: mu of phi0 into work[mu], then the equilibria of Eqs.
 // (bao_g_eq), (bao_f_eq) with p = 0 and S of u0 (Reading R8).
 template <int DIM>
-__global__ void __launch_bounds__(kThreads) bao_init_mu_kernel(const InitArgs a, BaoGeo<DIM> G) {
+__global__ void __launch_bounds__(kThreads) bao_init_mu_kernel(const InitArgs a, PassGeo<DIM> G) {
   using LS = typename Lattices<DIM>::S;
   const DevParams& P = a.p;
-  for (long long c = blockIdx.x * (long long)kThreads + threadIdx.x; c < a.N; c += (long long)gridDim.x * kThreads) {
-    int x, y, z;
-    G.coords(c, x, y, z);
+  pass_walk<DIM>(G, [&](const PassCell& cl) {
     float v[LS::Q];
-    gather<DIM, LS>(a.phi0, G, x, y, z, v);
+    gather<DIM, LS>(a.phi0, cl, v);
     const float pc = v[0];
-    a.work[a.N + c] = P.beta4 * (pc - P.phiH) * (pc - P.phiL) * (pc - P.phi0) - P.kappa * Sym<LS>::lap(v, pc);
-  }
+    a.work[a.N + cl.c] = P.beta4 * (pc - P.phiH) * (pc - P.phiL) * (pc - P.phi0) - P.kappa * Sym<LS>::lap(v, pc);
+  });
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(kThreads) bao_init_kernel(const InitArgs a, BaoGeo<DIM> G) {
+__global__ void __launch_bounds__(kThreads) bao_init_kernel(const InitArgs a, PassGeo<DIM> G) {
   using LG = typename Lattices<DIM>::G;
   using LF = typename Lattices<DIM>::F;
   using LS = typename Lattices<DIM>::S;
@@ -341,16 +321,15 @@ __global__ void __launch_bounds__(kThreads) bao_init_kernel(const InitArgs a, Ba
   const float* mu = a.work + a.N;
   float* g = static_cast<float*>(a.g);
   float* f = static_cast<float*>(a.f);
-  for (long long c = blockIdx.x * (long long)kThreads + threadIdx.x; c < a.N; c += (long long)gridDim.x * kThreads) {
-    int x, y, z;
-    G.coords(c, x, y, z);
+  pass_walk<DIM>(G, [&](const PassCell& cl) {
+    const unsigned c = cl.c;
     const float pc = a.phi0[c], muc = mu[c];
     const float rho = P.rhoL + P.drho_dphi * (pc - P.phiL);
     const float nu = viscosity(P, pc, rho);
     const float A_lks = (1.0f / P.inv_tau_phi) - 0.5f - bao_M(P, pc) * 3.0f / P.eta;
     const float B_lks = (1.0f / P.lks_itau) - 0.5f - 3.0f * nu;
     float vm[LS::Q];
-    gather<DIM, LS>(mu, G, x, y, z, vm);
+    gather<DIM, LS>(mu, cl, vm);
     float u[DIM], gmu[DIM], du[DIM][DIM], S[DIM][DIM];
     float usq = 0.0f, trS = 0.0f;
 #pragma unroll
@@ -359,7 +338,7 @@ __global__ void __launch_bounds__(kThreads) bao_init_kernel(const InitArgs a, Ba
       usq += u[k] * u[k];
       gmu[k] = Sym<LS>::grad(vm, k);
       float vu[LS::Q];
-      if (a.u0) gather<DIM, LS>(a.u0 + k * a.N, G, x, y, z, vu);
+      if (a.u0) gather<DIM, LS>(a.u0 + k * a.N, cl, vu);
 #pragma unroll
       for (int i = 0; i < DIM; ++i) du[k][i] = a.u0 ? Sym<LS>::grad(vu, i) : 0.0f;
     }
@@ -376,10 +355,10 @@ __global__ void __launch_bounds__(kThreads) bao_init_kernel(const InitArgs a, Ba
 #pragma unroll
       for (int k = 0; k < DIM; ++k) egm += (float)ecomp<LG>(q, k) * gmu[k];
       const float geq = LG::w(q) * (P.eta * muc + pc * gam_w<LG, DIM>(q, u, usq) + A_lks * P.eta * egm);
-      g[pop_ix<LG>(q, (unsigned)c)] = geq;
+      g[pop_ix<LG>(q, c)] = geq;
       sumeq += geq;
     }
-    g[pop_ix<LG>(0, (unsigned)c)] = pc - sumeq;
+    g[pop_ix<LG>(0, c)] = pc - sumeq;
 #pragma unroll
     for (int q = 0; q < LF::Q; ++q) {
       float SS = 0.0f;
@@ -387,34 +366,28 @@ __global__ void __launch_bounds__(kThreads) bao_init_kernel(const InitArgs a, Ba
       for (int i = 0; i < DIM; ++i)
 #pragma unroll
         for (int j = 0; j < DIM; ++j) SS += (float)(ecomp<LF>(q, i) * ecomp<LF>(q, j)) * S[i][j];
-      f[pop_ix<LF>(q, (unsigned)c)] =
+      f[pop_ix<LF>(q, c)] =
           LF::w(q) * (cs2 * rho * gam_w<LF, DIM>(q, u, usq) + 0.5f * rho * B_lks * (SS - cs2 * trS));
     }
-  }
-}
-
-int grid_for(long long N) {
-  const long long want = (N + kThreads - 1) / kThreads;
-  const long long cap = 8LL * 152;
-  return (int)(want < cap ? want : cap);
+  });
 }
 
 template <int DIM>
 void bao_step_dim(const StepArgs& a, cudaStream_t s) {
-  BaoGeo<DIM> G{a.p.nx, a.p.ny, DIM == 3 ? a.p.nz : 1};
-  const int grid = grid_for(a.N);
-  bao_phi_kernel<DIM><<<grid, kThreads, 0, s>>>(a);
-  bao_mu_kernel<DIM><<<grid, kThreads, 0, s>>>(a, G);
-  bao_macro_kernel<DIM><<<grid, kThreads, 0, s>>>(a, G);
-  if (!a.macro) bao_collide_kernel<DIM><<<grid, kThreads, 0, s>>>(a, G);
+  const PassGeo<DIM> G = pass_geo<DIM>(a.p.nx, a.p.ny, a.p.nz, num_sms());
+  const dim3 grid = G.grid(), block(kPassTX, kPassTY);
+  bao_phi_kernel<DIM><<<grid, block, 0, s>>>(a, G);
+  bao_mu_kernel<DIM><<<grid, block, 0, s>>>(a, G);
+  bao_macro_kernel<DIM><<<grid, block, 0, s>>>(a, G);
+  if (!a.macro) bao_collide_kernel<DIM><<<grid, block, 0, s>>>(a, G);
 }
 
 template <int DIM>
 void bao_init_dim(const InitArgs& a, cudaStream_t s) {
-  BaoGeo<DIM> G{a.p.nx, a.p.ny, DIM == 3 ? a.p.nz : 1};
-  const int grid = grid_for(a.N);
-  bao_init_mu_kernel<DIM><<<grid, kThreads, 0, s>>>(a, G);
-  bao_init_kernel<DIM><<<grid, kThreads, 0, s>>>(a, G);
+  const PassGeo<DIM> G = pass_geo<DIM>(a.p.nx, a.p.ny, a.p.nz, num_sms());
+  const dim3 grid = G.grid(), block(kPassTX, kPassTY);
+  bao_init_mu_kernel<DIM><<<grid, block, 0, s>>>(a, G);
+  bao_init_kernel<DIM><<<grid, block, 0, s>>>(a, G);
 }
 
 }  // namespace

@@ -15,30 +15,15 @@
 //   4. phi = phi* + (1 - lambda) R(phi*) / 2
 //   5. collision (the Liang2018 update of the fused step with Eq. Liu_G's
 //      mix), streaming, observables.
-// Work fields (N floats each): phi*, psi0, psi_a, psi_b, lambda, phi.
+// Work fields (N floats each): phi*, psi0, psi_a, psi_b, lambda, phi. Every
+// pass walks the domain as (x, y) tiles marching in z (pflb_pass.cuh).
 #include "pflb_init.cuh"
+#include "pflb_pass.cuh"
 
 namespace pflb {
 namespace {
 
-constexpr int kThreads = 256;
-
-template <int DIM>
-struct LiuGeo {
-  int nx, ny, nz;
-  __device__ __forceinline__ void coords(long long c, int& x, int& y, int& z) const {
-    x = (int)(c % nx);
-    y = (int)((c / nx) % ny);
-    z = DIM == 3 ? (int)(c / ((long long)nx * ny)) : 0;
-  }
-  __device__ __forceinline__ unsigned nb(int x, int y, int z, int ex, int ey, int ez) const {
-    int xn = x + ex, yn = y + ey, zn = z + ez;
-    xn = xn < 0 ? xn + nx : (xn >= nx ? xn - nx : xn);
-    yn = yn < 0 ? yn + ny : (yn >= ny ? yn - ny : yn);
-    if (DIM == 3) zn = zn < 0 ? zn + nz : (zn >= nz ? zn - nz : zn);
-    return (unsigned)(xn + nx * (yn + (DIM == 3 ? ny * zn : 0)));
-  }
-};
+constexpr int kThreads = kPassThreads;
 
 struct LiuWork {
   float *phis, *psi0, *psia, *psib, *lam, *phi;
@@ -48,14 +33,15 @@ __host__ __device__ inline LiuWork liu_work(float* w, long long N) {
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(kThreads) liu_predict_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(kThreads) liu_predict_kernel(const StepArgs a, PassGeo<DIM> G) {
   using LG = typename Lattices<DIM>::G;
   constexpr bool SKIP0 = DIM == 3;   // D3Q7 rest population of the Allen-Cahn families is zero
   const DevParams& P = a.p;
   const LiuWork W = liu_work(a.work, a.N);
   const float* g = static_cast<const float*>(a.g_src);
   const float lo = P.phiL + 0.01f, hi = P.phiH - 0.01f, dphi = P.phiH - P.phiL;
-  for (long long c = blockIdx.x * (long long)kThreads + threadIdx.x; c < a.N; c += (long long)gridDim.x * kThreads) {
+  pass_walk<DIM>(G, [&](const PassCell& cl) {
+    const unsigned c = cl.c;
     float v[LG::Q];
 #pragma unroll
     for (int q = 0; q < LG::Q; ++q) v[q] = (SKIP0 && q == 0) ? 0.0f : g[pop_ix<LG>(q, (unsigned)c)];
@@ -65,23 +51,23 @@ __global__ void __launch_bounds__(kThreads) liu_predict_kernel(const StepArgs a)
     const float psi = -0.25f * P.W_xi * logf(dphi / (pc - P.phiL) - 1.0f);
     W.psi0[c] = psi;
     W.psia[c] = psi;
-  }
+  });
 }
 
 // One Godunov step of the reinitialisation equation (Reading R22).
 template <int DIM>
-__global__ void __launch_bounds__(kThreads) liu_reinit_kernel(const float* psi_in, float* psi_out, const float* psi0,
-                                                              long long N, LiuGeo<DIM> G) {
-  for (long long c = blockIdx.x * (long long)kThreads + threadIdx.x; c < N; c += (long long)gridDim.x * kThreads) {
-    int x, y, z;
-    G.coords(c, x, y, z);
+__global__ void __launch_bounds__(kThreads) liu_reinit_kernel(const float* __restrict__ psi_in,
+                                                              float* __restrict__ psi_out,
+                                                              const float* __restrict__ psi0, PassGeo<DIM> G) {
+  pass_walk<DIM>(G, [&](const PassCell& cl) {
+    const unsigned c = cl.c;
     const float p = psi_in[c], p0 = psi0[c];
     const float S = p0 * rsqrtf(p0 * p0 + 1.0f);
     float g2p = 0.0f, g2m = 0.0f;
 #pragma unroll
     for (int ax = 0; ax < DIM; ++ax) {
-      const float pm = psi_in[G.nb(x, y, z, ax == 0 ? -1 : 0, ax == 1 ? -1 : 0, ax == 2 ? -1 : 0)];
-      const float pp = psi_in[G.nb(x, y, z, ax == 0 ? 1 : 0, ax == 1 ? 1 : 0, ax == 2 ? 1 : 0)];
+      const float pm = psi_in[cl.nb(ax == 0 ? -1 : 0, ax == 1 ? -1 : 0, ax == 2 ? -1 : 0)];
+      const float pp = psi_in[cl.nb(ax == 0 ? 1 : 0, ax == 1 ? 1 : 0, ax == 2 ? 1 : 0)];
       const float dm = p - pm, dp = pp - p;
       const float a1 = fmaxf(dm, 0.0f), b1 = fminf(dp, 0.0f);
       const float a2 = fminf(dm, 0.0f), b2 = fmaxf(dp, 0.0f);
@@ -90,18 +76,20 @@ __global__ void __launch_bounds__(kThreads) liu_reinit_kernel(const float* psi_i
     }
     const float grad = sqrtf(S > 0.0f ? g2p : g2m);
     psi_out[c] = p - 0.5f * S * (grad - 1.0f);
-  }
+  });
 }
 
 // lambda and the (1 - lambda)-weighted integrals I1, I2 (FP64 per block, one
 // atomic per block into acc).
 template <int DIM>
-__global__ void __launch_bounds__(kThreads) liu_gamma_kernel(const StepArgs a, const float* psi, double* acc) {
+__global__ void __launch_bounds__(kThreads) liu_gamma_kernel(const StepArgs a, const float* psi, double* acc,
+                                                             PassGeo<DIM> G) {
   const DevParams& P = a.p;
   const LiuWork W = liu_work(a.work, a.N);
   const float dmin = 3.0f * P.W_xi;
   double s1 = 0.0, s2 = 0.0;
-  for (long long c = blockIdx.x * (long long)kThreads + threadIdx.x; c < a.N; c += (long long)gridDim.x * kThreads) {
+  pass_walk<DIM>(G, [&](const PassCell& cl) {
+    const unsigned c = cl.c;
     const float lam = fabsf(psi[c]) < dmin ? 1.0f : 0.0f;
     W.lam[c] = lam;
     if (lam == 0.0f) {
@@ -109,17 +97,18 @@ __global__ void __launch_bounds__(kThreads) liu_gamma_kernel(const StepArgs a, c
       s1 += (double)(P.four_beta_over_kappa * (ps - P.phiH) * (ps - P.phiL) * (ps - P.phi0));
       s2 += (double)((P.phiH - ps) * (ps - P.phiL));
     }
-  }
+  });
   s1 = warp_sum(s1);
   s2 = warp_sum(s2);
   __shared__ double sh[2 * (kThreads / 32)];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tid = threadIdx.x + kPassTX * threadIdx.y;
+  const int lane = tid & 31, warp = tid >> 5;
   if (lane == 0) {
     sh[2 * warp] = s1;
     sh[2 * warp + 1] = s2;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     double t1 = 0.0, t2 = 0.0;
     for (int w = 0; w < kThreads / 32; ++w) {
       t1 += sh[2 * w];
@@ -131,20 +120,20 @@ __global__ void __launch_bounds__(kThreads) liu_gamma_kernel(const StepArgs a, c
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(kThreads) liu_phi_kernel(const StepArgs a, const double* acc) {
+__global__ void __launch_bounds__(kThreads) liu_phi_kernel(const StepArgs a, const double* acc, PassGeo<DIM> G) {
   const DevParams& P = a.p;
   const LiuWork W = liu_work(a.work, a.N);
   const double I2 = acc[1];
   const float gamma = I2 != 0.0 ? (float)(acc[0] / I2) : 0.0f;
-  for (long long c = blockIdx.x * (long long)kThreads + threadIdx.x; c < a.N; c += (long long)gridDim.x * kThreads) {
-    const float ps = W.phis[c];
-    W.phi[c] = ps + 0.5f * (1.0f - W.lam[c]) * nonlocal_R<FAM_LIU>(P, ps, gamma);
-  }
+  pass_walk<DIM>(G, [&](const PassCell& cl) {
+    const float ps = W.phis[cl.c];
+    W.phi[cl.c] = ps + 0.5f * (1.0f - W.lam[cl.c]) * nonlocal_R<FAM_LIU>(P, ps, gamma);
+  });
 }
 
 // Collision (Liang2018 with Eq. Liu_G's mix), streaming and observables.
 template <int DIM>
-__global__ void __launch_bounds__(kThreads) liu_collide_kernel(const StepArgs a, const double* acc, LiuGeo<DIM> G) {
+__global__ void __launch_bounds__(kThreads) liu_collide_kernel(const StepArgs a, const double* acc, PassGeo<DIM> G) {
   using LG = typename Lattices<DIM>::G;
   using LF = typename Lattices<DIM>::F;
   using LS = typename Lattices<DIM>::S;
@@ -157,15 +146,17 @@ __global__ void __launch_bounds__(kThreads) liu_collide_kernel(const StepArgs a,
   const double I2 = acc[1];
   const float gamma = I2 != 0.0 ? (float)(acc[0] / I2) : 0.0f;
   __shared__ double s_red[(kThreads / 32) * 10];
-  if (a.obs_zero != nullptr && blockIdx.x == 0 && threadIdx.x == 0) obs_zero_slot(a.obs_zero);
+  if (a.obs_zero != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&
+      threadIdx.y == 0)
+    obs_zero_slot(a.obs_zero);
   ObsPartial obs;
   obs_init(obs);
-  for (long long c = blockIdx.x * (long long)kThreads + threadIdx.x; c < a.N; c += (long long)gridDim.x * kThreads) {
-    int x, y, z;
-    G.coords(c, x, y, z);
+  pass_walk<DIM>(G, [&](const PassCell& cl) {
+    const unsigned c = cl.c;
+    const int x = cl.x, y = cl.y, z = cl.z;
     float nb[LS::Q];
 #pragma unroll
-    for (int q = 0; q < LS::Q; ++q) nb[q] = W.phi[G.nb(x, y, z, LS::ex(q), LS::ey(q), LS::ez(q))];
+    for (int q = 0; q < LS::Q; ++q) nb[q] = W.phi[cl.nb(LS::ex(q), LS::ey(q), LS::ez(q))];
     const float pc = nb[0];
     float gp[DIM];
 #pragma unroll
@@ -177,9 +168,9 @@ __global__ void __launch_bounds__(kThreads) liu_collide_kernel(const StepArgs a,
 #pragma unroll
     for (int q = 0; q < LF::Q; ++q)
       f[q] = a.parity == 0 ? fb[pop_ix<LF>(q, (unsigned)c)]
-                           : fb[pop_ix<LF>(LF::opp(q), G.nb(x, y, z, -LF::ex(q), -LF::ey(q), -LF::ez(q)))];
+                           : fb[pop_ix<LF>(LF::opp(q), cl.nb(-LF::ex(q), -LF::ey(q), -LF::ez(q)))];
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) phiu[k] = a.phiu[k * a.N + c];
+    for (int d = 0; d < DIM; ++d) phiu[d] = a.phiu[d * a.N + c];
     float u[DIM], rho, p;
     const float lam = W.lam[c];
     Cell<FAM_LIU, DIM>::collide(P, g, f, pc, W.phis[c], gp, lp, 0.0f, 0.0f, phiu, gamma, u, rho, p, lam);
@@ -203,19 +194,19 @@ __global__ void __launch_bounds__(kThreads) liu_collide_kernel(const StepArgs a,
 #pragma unroll
       for (int k = 0; k < DIM; ++k) a.out_u[k * a.N + c] = u[k];
       a.out_p[c] = p;
-      continue;
+      return;
     }
 #pragma unroll
     for (int k = 0; k < DIM; ++k) a.phiu[k * a.N + c] = phiu[k];
 #pragma unroll
     for (int q = 0; q < LG::Q; ++q)
-      if (!(SKIP0 && q == 0)) gd[pop_ix<LG>(q, G.nb(x, y, z, LG::ex(q), LG::ey(q), LG::ez(q)))] = g[q];
+      if (!(SKIP0 && q == 0)) gd[pop_ix<LG>(q, cl.nb(LG::ex(q), LG::ey(q), LG::ez(q)))] = g[q];
 #pragma unroll
     for (int q = 0; q < LF::Q; ++q) {
       if (a.parity == 0) fb[pop_ix<LF>(LF::opp(q), (unsigned)c)] = f[q];
-      else fb[pop_ix<LF>(q, G.nb(x, y, z, LF::ex(q), LF::ey(q), LF::ez(q)))] = f[q];
+      else fb[pop_ix<LF>(q, cl.nb(LF::ex(q), LF::ey(q), LF::ez(q)))] = f[q];
     }
-  }
+  });
   if (obs.mn <= obs.mx) {
     const float r1 = P.rhoL + P.drho_dphi * (obs.mn - P.phiL), r2 = P.rhoL + P.drho_dphi * (obs.mx - P.phiL);
     if (!(isfinite(obs.s_hi) && isfinite(obs.ke) && r1 > 0.0f && r2 > 0.0f)) obs.bad = 1u;
@@ -223,23 +214,17 @@ __global__ void __launch_bounds__(kThreads) liu_collide_kernel(const StepArgs a,
   obs_block_commit(obs, a.obs_slot, s_red);
 }
 
-int grid_for(long long N) {
-  const long long want = (N + kThreads - 1) / kThreads;
-  const long long cap = 8LL * 152;
-  return (int)(want < cap ? want : cap);
-}
-
 template <int DIM>
 void liu_step_dim(const StepArgs& a, cudaStream_t s) {
-  LiuGeo<DIM> G{a.p.nx, a.p.ny, DIM == 3 ? a.p.nz : 1};
-  const int grid = grid_for(a.N);
+  const PassGeo<DIM> G = pass_geo<DIM>(a.p.nx, a.p.ny, a.p.nz, num_sms());
+  const dim3 grid = G.grid(), block(kPassTX, kPassTY);
   const LiuWork W = liu_work(a.work, a.N);
-  liu_predict_kernel<DIM><<<grid, kThreads, 0, s>>>(a);
+  liu_predict_kernel<DIM><<<grid, block, 0, s>>>(a, G);
   const int nit = (int)ceilf(2.0f * 3.0f * a.p.W_xi);
   const float* in = W.psia;
   float* out = W.psib;
   for (int it = 0; it < nit; ++it) {
-    liu_reinit_kernel<DIM><<<grid, kThreads, 0, s>>>(in, out, W.psi0, a.N, G);
+    liu_reinit_kernel<DIM><<<grid, block, 0, s>>>(in, out, W.psi0, G);
     const float* t = out;
     out = const_cast<float*>(in);
     in = t;
@@ -247,9 +232,9 @@ void liu_step_dim(const StepArgs& a, cudaStream_t s) {
   // gamma_acc holds this step's (I1, I2) pair, zeroed here
   double* acc = const_cast<double*>(a.gamma_acc);
   cudaMemsetAsync(acc, 0, 2 * sizeof(double), s);
-  liu_gamma_kernel<DIM><<<grid, kThreads, 0, s>>>(a, in, acc);
-  liu_phi_kernel<DIM><<<grid, kThreads, 0, s>>>(a, acc);
-  liu_collide_kernel<DIM><<<grid, kThreads, 0, s>>>(a, acc, G);
+  liu_gamma_kernel<DIM><<<grid, block, 0, s>>>(a, in, acc, G);
+  liu_phi_kernel<DIM><<<grid, block, 0, s>>>(a, acc, G);
+  liu_collide_kernel<DIM><<<grid, block, 0, s>>>(a, acc, G);
 }
 
 }  // namespace

@@ -61,9 +61,20 @@ def _gather_patches(state, n, cells, r):
     return np.stack(out)
 
 
-@pytest.mark.parametrize("storage,tol", [(0, 2e-6), (1, 1.5e-3)], ids=["fp32", "fp16"])
-def test_hit_512_sampled_one_step(hit512, storage, tol):
+VARIANTS = {"d3q19": dict(), "d3q27_mrt": dict(lattice_f=27, collision=1, mrt_s_bulk=1.0, mrt_s_ho=1.0),
+            "bao2024": dict(family=C.BAO2024)}
+
+
+@pytest.mark.parametrize("variant,storage,tol", [("d3q19", 0, 2e-6), ("d3q19", 1, 1.5e-3),
+                                                 ("d3q27_mrt", 0, 2e-6), ("bao2024", 0, 2e-6)],
+                         ids=["fp32", "fp16", "d3q27_mrt_fp32", "bao2024_fp32"])
+def test_hit_512_sampled_one_step(hit512, variant, storage, tol):
+    """One step of the full 512^3 workload at 53 sampled cells (block seams and
+    the periodic wrap included), each recomputed by the oracle on a periodic
+    patch around the cell (radius 2; 4 for Bao2024, whose pressure gradient
+    acts on stencils of mu)."""
     P, phi, u = hit512
+    P = dict(P, **VARIANTS[variant])
     n = P["nx"]
     sim = pflb.Sim(dict(P, storage=storage))
     sim.init(phi.contiguous(), u.contiguous())
@@ -76,14 +87,15 @@ def test_hit_512_sampled_one_step(hit512, storage, tol):
     cells = [tuple(int(v) for v in rng.integers(0, n, size=3)) for _ in range(48)]
     # include block seams and the periodic wrap
     cells += [(0, 0, 0), (n - 1, n - 1, n - 1), (31, 7, 63), (32, 8, 64), (511, 0, 255)]
-    r = 2
+    r = 4 if variant == "bao2024" else 2
     patches = _gather_patches(before, n, cells, r)
     sim.step(1)
     sim.sync()
     after = torch.empty(sim.state_floats(), device="cuda")
     sim.save(after)
     after = after.view(nf, n, n, n)
-    lg, lf, _ = O.lattices_for(3)
+    sim.close()
+    lg, lf, _ = O.lattices_of(P)
     Pp = dict(P, nx=2 * r + 1, ny=2 * r + 1, nz=2 * r + 1)
     scale = float(before.abs().max().item())
     worst = 0.0
