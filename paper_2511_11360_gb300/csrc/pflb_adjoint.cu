@@ -30,9 +30,11 @@ int grid_for(long long N) {
 template <int DIM>
 void launch_reverse_step(const AdjArgs& a, cudaStream_t s) {
   const int grid = grid_for(a.N);
+  const PassGeo<DIM> G{a.nx, a.ny, a.nz, a.zc};
+  const dim3 wgrid = G.grid(), wblock(kPassTX, kPassTY);
   adj_phi_kernel<DIM><<<grid, 256, 0, s>>>(a.state, const_cast<float*>(a.phi), a.N);
-  adj_local_kernel<DIM><<<grid, 256, 0, s>>>(a);
-  adj_stencil_kernel<DIM><<<grid, 256, 0, s>>>(a);
+  adj_local_kernel<DIM><<<wgrid, wblock, 0, s>>>(a);
+  adj_stencil_kernel<DIM><<<wgrid, wblock, 0, s>>>(a);
 }
 
 }  // namespace
@@ -151,6 +153,7 @@ extern "C" int pflb_adjoint(pflb_handle* h, int64_t nsteps, int32_t checkpoint_e
   a.nx = p.nx;
   a.ny = p.ny;
   a.nz = dim == 3 ? p.nz : 1;
+  a.zc = dim == 3 ? pass_geo<3>(p.nx, p.ny, p.nz, num_sms()).zc : 1;
   a.N = N;
   a.phi = phi;
   a.aux = aux;

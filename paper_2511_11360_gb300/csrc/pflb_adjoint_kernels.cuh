@@ -28,6 +28,7 @@
 // Arithmetic is FP32; the parameter sums are FP64.
 #pragma once
 
+#include "pflb_pass.cuh"
 #include "pflb_step.cuh"
 
 namespace pflb {
@@ -35,6 +36,7 @@ namespace pflb {
 struct AdjArgs {
   DevParams p;
   int nx, ny, nz;
+  int zc;                 // planes per block of the (x, y)-tile walk
   long long N;
   const float* state;     // canonical state of step n: g (QG x N) then f (QF x N)
   const float* phi;       // phi of that state (N)
@@ -45,20 +47,6 @@ struct AdjArgs {
   float dbeta4_dsigma, dkappa_dsigma;  // beta4 and kappa are linear in sigma
   float W;
 };
-
-__device__ __forceinline__ long long adj_nbr(long long i, int dx, int dy, int dz, int nx, int ny, int nz) {
-  int x = (int)(i % nx);
-  long long r = i / nx;
-  int y = (int)(r % ny);
-  int z = (int)(r / ny);
-  x += dx;
-  y += dy;
-  z += dz;
-  x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
-  y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-  z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
-  return (long long)x + (long long)nx * ((long long)y + (long long)ny * z);
-}
 
 template <typename L>
 __device__ __forceinline__ float edot(int q, const float* v, int dim) {
@@ -79,16 +67,17 @@ __device__ __forceinline__ void block_add3(double a, double b, double c, double*
   a = warp_sum(a);
   b = warp_sum(b);
   c = warp_sum(c);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y, nthreads = blockDim.x * blockDim.y;
+  const int lane = tid & 31, warp = tid >> 5;
   if (lane == 0) {
     s[3 * warp] = a;
     s[3 * warp + 1] = b;
     s[3 * warp + 2] = c;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     double t0 = 0.0, t1 = 0.0, t2 = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    for (int w = 0; w < (nthreads >> 5); ++w) {
       t0 += s[3 * w];
       t1 += s[3 * w + 1];
       t2 += s[3 * w + 2];
@@ -113,7 +102,7 @@ __global__ void adj_phi_kernel(const float* __restrict__ state, float* __restric
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(256) adj_local_kernel(const AdjArgs a) {
+__global__ void __launch_bounds__(256, 2) adj_local_kernel(const AdjArgs a) {
   using LG = typename Lattices<DIM>::G;
   using LF = typename Lattices<DIM>::F;
   using LS = typename Lattices<DIM>::S;
@@ -121,13 +110,25 @@ __global__ void __launch_bounds__(256) adj_local_kernel(const AdjArgs a) {
   const DevParams& P = a.p;
   const long long N = a.N;
   double accM = 0.0, accS = 0.0, accW = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+  const PassGeo<DIM> G{a.nx, a.ny, a.nz, a.zc};
+  const int lane = threadIdx.x;   // the x lane: a warp covers 32 consecutive cells of one row
+  pass_walk<DIM>(G, [&](const PassCell& cl) {
+    const long long i = cl.c;
+    // The cell is latency-bound (one cell per thread, many dependent loads):
+    // ask L2 for the rows of the next plane now. Lane q < QG + QF takes the
+    // row of array q of the state and of lambda_in (the pulled lambda of the
+    // next plane mostly lies in that row).
+    if (DIM == 3 && cl.z + 1 < a.nz && lane < QG + QF) {
+      const long long rn = (long long)(cl.c - (unsigned)lane) + (long long)a.nx * a.ny + (long long)lane * N;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a.state + rn));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a.lam_in + rn));
+    }
     // ---- forward recomputation at the cell
     const float phi = a.phi[i];
     float gp[3] = {0.0f, 0.0f, 0.0f}, lp = 0.0f;
 #pragma unroll
     for (int q = 1; q < QS; ++q) {
-      const float nb = a.phi[adj_nbr(i, LS::ex(q), LS::ey(q), LS::ez(q), a.nx, a.ny, a.nz)];
+      const float nb = a.phi[cl.nb(LS::ex(q), LS::ey(q), LS::ez(q))];
 #pragma unroll
       for (int k = 0; k < DIM; ++k)
         if (ecomp_adj<LS>(q, k)) gp[k] += LS::w(q) * (float)ecomp_adj<LS>(q, k) * nb;
@@ -136,15 +137,14 @@ __global__ void __launch_bounds__(256) adj_local_kernel(const AdjArgs a) {
 #pragma unroll
     for (int k = 0; k < DIM; ++k) gp[k] *= 3.0f;
     lp *= 6.0f;
-    float f[QF];
     float sumf = 0.0f, mom[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int q = 0; q < QF; ++q) {
-      f[q] = a.state[(QG + q) * N + i];
-      sumf += f[q];
+      const float fq = a.state[(QG + q) * N + i];
+      sumf += fq;
 #pragma unroll
       for (int k = 0; k < DIM; ++k)
-        if (ecomp_adj<LF>(q, k)) mom[k] += (float)ecomp_adj<LF>(q, k) * f[q];
+        if (ecomp_adj<LF>(q, k)) mom[k] += (float)ecomp_adj<LF>(q, k) * fq;
     }
     const float rho = P.rhoL;
     const float inv_rho = 1.0f / rho;
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256) adj_local_kernel(const AdjArgs a) {
     float tphibar = 0.0f;
 #pragma unroll
     for (int q = 0; q < QG; ++q) {
-      const long long src = adj_nbr(i, LG::ex(q), LG::ey(q), LG::ez(q), a.nx, a.ny, a.nz);
+      const long long src = cl.nb(LG::ex(q), LG::ey(q), LG::ez(q));
       const float ls = a.lam_in[q * N + src];          // lambda of g*_q(x)
       const float w = LG::w(q);
       const float gq = a.state[q * N + i];
@@ -206,12 +206,10 @@ __global__ void __launch_bounds__(256) adj_local_kernel(const AdjArgs a) {
       tphibar += ls * ((gq - geq) + 0.5f * Gq) * itp * itp;
     }
     float itaubar = 0.0f, sumfbar = 0.0f, Ftbar[3] = {0.0f, 0.0f, 0.0f};
-    float lsf[QF];
 #pragma unroll
     for (int q = 0; q < QF; ++q) {
-      const long long src = adj_nbr(i, LF::ex(q), LF::ey(q), LF::ez(q), a.nx, a.ny, a.nz);
+      const long long src = cl.nb(LF::ex(q), LF::ey(q), LF::ez(q));
       const float ls = a.lam_in[(QG + q) * N + src];   // lambda of f*_q(x)
-      lsf[q] = ls;
       const float w = LF::w(q);
       const float eu = edot<LF>(q, u, DIM);
       const float feq = w * (sumf + 3.0f * eu + 4.5f * eu * eu - 1.5f * usq);
@@ -225,7 +223,8 @@ __global__ void __launch_bounds__(256) adj_local_kernel(const AdjArgs a) {
         ubar[k] += feqbar * w * (3.0f * e + 9.0f * eu * e - 3.0f * u[k]);
         Ftbar[k] += Fqbar * 3.0f * w * e;
       }
-      itaubar += ls * (-(f[q] - feq) - 0.5f * Fq);
+      // f_q read again (cached) rather than held in registers across the cell
+      itaubar += ls * (-(a.state[(QG + q) * N + i] - feq) - 0.5f * Fq);
     }
     // F = F_o + A rho u; u = (mom + F_o/(2 rho)) / (1 - A/2)
     float Fobar[3], mombar[3];
@@ -265,7 +264,9 @@ __global__ void __launch_bounds__(256) adj_local_kernel(const AdjArgs a) {
     // f: through sum f and sum e f
 #pragma unroll
     for (int q = 0; q < QF; ++q) {
-      float v = lsf[q] * (1.0f - itau) + sumfbar;
+      // lambda of f*_q(x) read again (cached) rather than held in registers
+      const float ls = a.lam_in[(QG + q) * N + cl.nb(LF::ex(q), LF::ey(q), LF::ez(q))];
+      float v = ls * (1.0f - itau) + sumfbar;
 #pragma unroll
       for (int k = 0; k < DIM; ++k)
         if (ecomp_adj<LF>(q, k)) v += (float)ecomp_adj<LF>(q, k) * mombar[k];
@@ -280,7 +281,7 @@ __global__ void __launch_bounds__(256) adj_local_kernel(const AdjArgs a) {
     accM += 3.0 * (double)tphibar;
     accS += (double)beta4bar * a.dbeta4_dsigma + (double)kappabar * a.dkappa_dsigma;
     accW += ((double)(-beta4bar * P.beta4) + (double)(kappabar * P.kappa) - (double)(kbar * kk)) / (double)a.W;
-  }
+  });
   block_add3(accM, accS, accW, a.acc);
 }
 
@@ -292,11 +293,13 @@ __global__ void __launch_bounds__(256) adj_stencil_kernel(const AdjArgs a) {
   constexpr int QG = LG::Q, QS = LS::Q;
   const long long N = a.N;
   const float wrest = 1.0f - LS::w(0);
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+  const PassGeo<DIM> G{a.nx, a.ny, a.nz, a.zc};
+  pass_walk<DIM>(G, [&](const PassCell& cl) {
+    const long long i = cl.c;
     float t = a.aux[i] - 6.0f * wrest * a.aux[(1 + DIM) * N + i];
 #pragma unroll
     for (int q = 1; q < QS; ++q) {
-      const long long y = adj_nbr(i, -LS::ex(q), -LS::ey(q), -LS::ez(q), a.nx, a.ny, a.nz);
+      const long long y = cl.nb(-LS::ex(q), -LS::ey(q), -LS::ez(q));
       float eg = 0.0f;
 #pragma unroll
       for (int k = 0; k < DIM; ++k)
@@ -305,7 +308,7 @@ __global__ void __launch_bounds__(256) adj_stencil_kernel(const AdjArgs a) {
     }
 #pragma unroll
     for (int q = 0; q < QG; ++q) a.lam_out[q * N + i] += t;
-  }
+  });
 }
 
 // Objective pieces of a phi field: sum phi, sum x_k phi, smooth volume.

@@ -545,9 +545,10 @@ double pflb_bytes_per_update(const pflb_handle* h) {
     b += 4.0 * (qg + 1) + 8.0 + 4.0 * h->QF + 8.0 + 4.0 * (h->dim + 1) + 4.0 * (3 + h->dim);
   }
   if (h->family == PFLB_HAC_LIU2023) {
-    // the passes: g read for phi*, phi* psi0 psi written; per reinitialisation
-    // step psi and psi0 read and psi written; lambda written, phi* read twice,
-    // lambda read twice, phi written and read (field words of 4 bytes)
+    // the passes: g read for phi*, phi* S(psi0) psi written; per
+    // reinitialisation step psi and S(psi0) read and psi written; lambda
+    // written, phi* read twice, lambda read twice, phi written and read
+    // (field words of 4 bytes)
     const double nit = std::ceil(6.0 * h->prm.W);
     b += 4.0 * qg + 12.0 + 12.0 * nit + 12.0 + 12.0 + 12.0;
   }

@@ -1,5 +1,6 @@
 // Auxiliary kernels: the domain integrals of the nonlocal Lagrange
 // multiplier and the copy between storage and the canonical FP32 state.
+#include "pflb_pass.cuh"
 #include "pflb_step.cuh"
 
 namespace pflb {
@@ -85,7 +86,7 @@ void gamma_sums(int dim, int storage, const GammaArgs& a, cudaStream_t s) {
 // reads: slot q of x before an even step; before an odd step slot opp(q) of
 // x - e_q, or slot q of x itself where x - e_q lies beyond a wall.
 template <int DIM, typename T, int LAT>
-__global__ void canon_kernel(const CanonArgs a) {
+__global__ void __launch_bounds__(kPassThreads) canon_kernel(const CanonArgs a, const PassGeo<DIM> G) {
   using LG = typename Lattices<DIM, LAT>::G;
   using LF = typename Lattices<DIM, LAT>::F;
   constexpr int QG = LG::Q, QF = LF::Q;
@@ -94,11 +95,9 @@ __global__ void canon_kernel(const CanonArgs a) {
   const int nx = P.nx, ny = P.ny, nz = (DIM == 3) ? P.nz : 1;
   T* g = static_cast<T*>(a.g);
   T* f = static_cast<T*>(a.f);
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(idx % nx);
-    const int y = (int)((idx / nx) % ny);
-    const int z = (int)(idx / ((long long)nx * ny));
+  pass_walk<DIM>(G, [&](const PassCell& cl) {
+    const long long idx = cl.c;
+    const int x = cl.x, y = cl.y, z = cl.z;
 #pragma unroll
     for (int q = 0; q < QG; ++q) {
       float* sp = a.state + (long long)q * N + idx;
@@ -142,16 +141,15 @@ __global__ void canon_kernel(const CanonArgs a) {
         else *pp = *sp;
       }
     }
-  }
+  });
 }
 
 template <int DIM, typename T>
 static void launch_canon(const CanonArgs& a, cudaStream_t s) {
-  long long want = (a.N + 255) / 256;
-  long long cap = 16LL * sm_count();
-  const unsigned grid = (unsigned)(want < cap ? want : cap);
-  if (DIM == 3 && a.p.lat == 1) canon_kernel<DIM, T, (DIM == 3 ? 1 : 0)><<<grid, 256, 0, s>>>(a);
-  else canon_kernel<DIM, T, 0><<<grid, 256, 0, s>>>(a);
+  const PassGeo<DIM> G = pass_geo<DIM>(a.p.nx, a.p.ny, a.p.nz, sm_count());
+  const dim3 grid = G.grid(), block(kPassTX, kPassTY);
+  if (DIM == 3 && a.p.lat == 1) canon_kernel<DIM, T, (DIM == 3 ? 1 : 0)><<<grid, block, 0, s>>>(a, G);
+  else canon_kernel<DIM, T, 0><<<grid, block, 0, s>>>(a, G);
 }
 
 void canon_copy(int dim, int storage, const CanonArgs& a, cudaStream_t s) {

@@ -9,14 +9,15 @@
 //      (phi* clamped to [phi_L + 0.01, phi_H - 0.01])
 //   2. ceil(2 d_min) pseudo-time steps (dt' = 1/2) of the reinitialisation
 //      equation d psi/dt' + S(psi0)(|grad psi| - 1) = 0, first-order Godunov
-//      upwinding, S(psi0) = psi0 / sqrt(psi0^2 + 1)
+//      upwinding, S(psi0) = psi0 / sqrt(psi0^2 + 1) (formed once by the
+//      predictor)
 //   3. lambda = [|psi| < d_min]; the (1 - lambda)-weighted integrals of Eq.
 //      (lagrange_multiplier) in FP64
 //   4. phi = phi* + (1 - lambda) R(phi*) / 2
 //   5. collision (the Liang2018 update of the fused step with Eq. Liu_G's
 //      mix), streaming, observables.
-// Work fields (N floats each): phi*, psi0, psi_a, psi_b, lambda, phi. Every
-// pass walks the domain as (x, y) tiles marching in z (pflb_pass.cuh).
+// Work fields (N floats each): phi*, S(psi0), psi_a, psi_b, lambda, phi.
+// Every pass walks the domain as (x, y) tiles marching in z (pflb_pass.cuh).
 #include "pflb_init.cuh"
 #include "pflb_pass.cuh"
 
@@ -26,7 +27,7 @@ namespace {
 constexpr int kThreads = kPassThreads;
 
 struct LiuWork {
-  float *phis, *psi0, *psia, *psib, *lam, *phi;
+  float *phis, *s0, *psia, *psib, *lam, *phi;
 };
 __host__ __device__ inline LiuWork liu_work(float* w, long long N) {
   return LiuWork{w, w + N, w + 2 * N, w + 3 * N, w + 4 * N, w + 5 * N};
@@ -49,57 +50,103 @@ __global__ void __launch_bounds__(kThreads) liu_predict_kernel(const StepArgs a,
     W.phis[c] = ps;
     const float pc = fminf(fmaxf(ps, lo), hi);
     const float psi = -0.25f * P.W_xi * logf(dphi / (pc - P.phiL) - 1.0f);
-    W.psi0[c] = psi;
+    W.s0[c] = psi * rsqrtf(psi * psi + 1.0f);
     W.psia[c] = psi;
   });
 }
 
-// One Godunov step of the reinitialisation equation (Reading R22).
+// One first-order Godunov step (dt' = 1/2) of the reinitialisation equation
+// at a cell from its value p, its axis neighbours (minus, plus) and
+// S = S(psi0) (Reading R22). Upwinding per axis: for S > 0,
+// max(max(D-, 0)^2, min(D+, 0)^2), for S <= 0, max(min(D-, 0)^2, max(D+, 0)^2)
+// with D- = p - p(x - e), D+ = p(x + e) - p; with sg = sign(S) both read
+// max(max(sg D-, 0)^2, max(-sg D+, 0)^2) (the squares lose the sign exactly).
+template <int DIM>
+__device__ __forceinline__ float liu_godunov(float p, const float (&nm)[DIM], const float (&np)[DIM], float S) {
+  const float sg = S > 0.0f ? 1.0f : -1.0f;
+  float g2 = 0.0f;
+#pragma unroll
+  for (int ax = 0; ax < DIM; ++ax) {
+    const float a = fmaxf(sg * (p - nm[ax]), 0.0f), b = fmaxf(sg * (p - np[ax]), 0.0f);
+    g2 += fmaxf(a * a, b * b);
+  }
+  return p - 0.5f * S * (sqrtf(g2) - 1.0f);
+}
+
+// One pseudo-time step over the domain: the (x, y)-tile walk of the other
+// passes, with psi of the z neighbours carried in registers along the march.
 template <int DIM>
 __global__ void __launch_bounds__(kThreads) liu_reinit_kernel(const float* __restrict__ psi_in,
                                                               float* __restrict__ psi_out,
-                                                              const float* __restrict__ psi0, PassGeo<DIM> G) {
-  pass_walk<DIM>(G, [&](const PassCell& cl) {
-    const unsigned c = cl.c;
-    const float p = psi_in[c], p0 = psi0[c];
-    const float S = p0 * rsqrtf(p0 * p0 + 1.0f);
-    float g2p = 0.0f, g2m = 0.0f;
+                                                              const float* __restrict__ s0, PassGeo<DIM> G) {
+  const int x = (int)(blockIdx.x * kPassTX + threadIdx.x), y = (int)(blockIdx.y * kPassTY + threadIdx.y);
+  if (x >= G.nx || y >= G.ny) return;
+  const unsigned nx = (unsigned)G.nx;
+  const unsigned xm = (unsigned)(x == 0 ? G.nx - 1 : x - 1), xp = (unsigned)(x == G.nx - 1 ? 0 : x + 1);
+  const unsigned ym = nx * (unsigned)(y == 0 ? G.ny - 1 : y - 1), yp = nx * (unsigned)(y == G.ny - 1 ? 0 : y + 1);
+  const unsigned xc = (unsigned)x, yc = nx * (unsigned)y;
+  if constexpr (DIM == 2) {
+    const unsigned c = xc + yc;
+    const float nm[2] = {psi_in[xm + yc], psi_in[xc + ym]};
+    const float np[2] = {psi_in[xp + yc], psi_in[xc + yp]};
+    psi_out[c] = liu_godunov<2>(psi_in[c], nm, np, s0[c]);
+  } else {
+    const unsigned nxy = nx * (unsigned)G.ny;
+    const int z0 = (int)blockIdx.z * G.zc, z1 = min(G.nz, z0 + G.zc);
+    float pzm = psi_in[xc + yc + nxy * (unsigned)(z0 == 0 ? G.nz - 1 : z0 - 1)];
+    float pzc = psi_in[xc + yc + nxy * (unsigned)z0];
+    // U planes per round, all of their loads issued before any update (the
+    // update is cheap, so the march is bound by how many loads are in flight);
+    // planes past the run repeat its last plane and are not stored
+    constexpr int U = 4;
+    for (int z = z0; z < z1; z += U) {
+      float zn[U], vxm[U], vxp[U], vym[U], vyp[U], sv[U];
 #pragma unroll
-    for (int ax = 0; ax < DIM; ++ax) {
-      const float pm = psi_in[cl.nb(ax == 0 ? -1 : 0, ax == 1 ? -1 : 0, ax == 2 ? -1 : 0)];
-      const float pp = psi_in[cl.nb(ax == 0 ? 1 : 0, ax == 1 ? 1 : 0, ax == 2 ? 1 : 0)];
-      const float dm = p - pm, dp = pp - p;
-      const float a1 = fmaxf(dm, 0.0f), b1 = fminf(dp, 0.0f);
-      const float a2 = fminf(dm, 0.0f), b2 = fmaxf(dp, 0.0f);
-      g2p += fmaxf(a1 * a1, b1 * b1);
-      g2m += fmaxf(a2 * a2, b2 * b2);
+      for (int u = 0; u < U; ++u) {
+        const int zz = min(z + u, z1 - 1);
+        const unsigned oz = nxy * (unsigned)zz, ozp = nxy * (unsigned)(zz == G.nz - 1 ? 0 : zz + 1);
+        zn[u] = psi_in[xc + yc + ozp];
+        vxm[u] = psi_in[xm + yc + oz];
+        vxp[u] = psi_in[xp + yc + oz];
+        vym[u] = psi_in[xc + ym + oz];
+        vyp[u] = psi_in[xc + yp + oz];
+        sv[u] = s0[xc + yc + oz];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (z + u < z1) {
+          const float nm[3] = {vxm[u], vym[u], pzm};
+          const float np[3] = {vxp[u], vyp[u], zn[u]};
+          psi_out[xc + yc + nxy * (unsigned)(z + u)] = liu_godunov<3>(pzc, nm, np, sv[u]);
+          pzm = pzc;
+          pzc = zn[u];
+        }
+      }
     }
-    const float grad = sqrtf(S > 0.0f ? g2p : g2m);
-    psi_out[c] = p - 0.5f * S * (grad - 1.0f);
-  });
+  }
 }
 
-// lambda and the (1 - lambda)-weighted integrals I1, I2 (FP64 per block, one
-// atomic per block into acc).
+// lambda and the (1 - lambda)-weighted integrals I1, I2 (compensated FP32 per
+// thread, FP64 across threads, one atomic per block into acc).
 template <int DIM>
 __global__ void __launch_bounds__(kThreads) liu_gamma_kernel(const StepArgs a, const float* psi, double* acc,
                                                              PassGeo<DIM> G) {
   const DevParams& P = a.p;
   const LiuWork W = liu_work(a.work, a.N);
   const float dmin = 3.0f * P.W_xi;
-  double s1 = 0.0, s2 = 0.0;
+  float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;   // per-thread compensated FP32 sums
   pass_walk<DIM>(G, [&](const PassCell& cl) {
     const unsigned c = cl.c;
     const float lam = fabsf(psi[c]) < dmin ? 1.0f : 0.0f;
     W.lam[c] = lam;
     if (lam == 0.0f) {
       const float ps = W.phis[c];
-      s1 += (double)(P.four_beta_over_kappa * (ps - P.phiH) * (ps - P.phiL) * (ps - P.phi0));
-      s2 += (double)((P.phiH - ps) * (ps - P.phiL));
+      comp_add(h1, l1, P.four_beta_over_kappa * (ps - P.phiH) * (ps - P.phiL) * (ps - P.phi0));
+      comp_add(h2, l2, (P.phiH - ps) * (ps - P.phiL));
     }
   });
-  s1 = warp_sum(s1);
-  s2 = warp_sum(s2);
+  const double s1 = warp_sum((double)h1 + (double)l1);
+  const double s2 = warp_sum((double)h2 + (double)l2);
   __shared__ double sh[2 * (kThreads / 32)];
   const int tid = threadIdx.x + kPassTX * threadIdx.y;
   const int lane = tid & 31, warp = tid >> 5;
@@ -223,11 +270,14 @@ void liu_step_dim(const StepArgs& a, cudaStream_t s) {
   const int nit = (int)ceilf(2.0f * 3.0f * a.p.W_xi);
   const float* in = W.psia;
   float* out = W.psib;
-  for (int it = 0; it < nit; ++it) {
-    liu_reinit_kernel<DIM><<<grid, block, 0, s>>>(in, out, W.psi0, G);
+  auto swap = [&] {
     const float* t = out;
     out = const_cast<float*>(in);
     in = t;
+  };
+  for (int it = 0; it < nit; ++it) {
+    liu_reinit_kernel<DIM><<<grid, block, 0, s>>>(in, out, W.s0, G);
+    swap();
   }
   // gamma_acc holds this step's (I1, I2) pair, zeroed here
   double* acc = const_cast<double*>(a.gamma_acc);
