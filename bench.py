@@ -289,8 +289,16 @@ def adjoint_variant(n=128, nsteps=2000):
 
     h = 1e-2 * P["sigma"]
     fd = (J_of(P["sigma"] + h) - J_of(P["sigma"] - h)) / (2 * h)
+    # Algorithmic bytes per cell and step of the whole job (3D, K = checkpoint
+    # interval): forward step 200 + checkpoint copy 204 / K; recomputation:
+    # canonical copy 204 + step 200 (K - 1) / K + checkpoint load 204 / K;
+    # reverse: adj_phi 32 + adj_local 336 + adj_stencil 76.
+    K = g["checkpoint_every"]
+    bpc = 200.0 + 204.0 / K + 204.0 + 200.0 * (K - 1) / K + 204.0 / K + 32.0 + 336.0 + 76.0
+    peak, _ = _peaks()
     return {"workload": "3D droplet in Taylor-Green vortex %d^3 periodic, R=24, W=4, u0=0.02, Fakhari2017 FP32" % n,
             "steps": nsteps, "seconds": t, "forward_plus_reverse_GLUPS": n ** 3 * nsteps / t / 1e9,
+            "bytes_per_cell_step": bpc, "roofline_frac": bpc * n ** 3 * nsteps / t / 1e9 / peak,
             "checkpoint_every": g["checkpoint_every"], "checkpoints": g["checkpoints"],
             "J": g["J"], "dJ_dM": g["dJ_dM"], "dJ_dsigma": g["dJ_dsigma"], "dJ_dW": g["dJ_dW"],
             "dJ_dsigma_central_difference_fp32": fd, "max_abs_dJ_du0": float(du0.abs().max())}

@@ -105,6 +105,13 @@ __global__ void __launch_bounds__(kThreads) bao_macro_kernel(const StepArgs a, P
   pass_walk<DIM>(G, [&](const PassCell& cl) {
     const unsigned c = cl.c;
     const int x = cl.x, y = cl.y, z = cl.z;
+    // next plane: the f lines, then the phi and mu rows
+    const long long rn = next_plane_row<DIM>(G, cl);
+    if (rn >= 0) {
+      const int l = threadIdx.x;
+      if (l < LF::Q) prefetch_l2(group_line<LF>(fb, rn, l));
+      else if (l < LF::Q + 2) prefetch_l2(a.work + (size_t)(l - LF::Q) * a.N + rn);
+    }
     // incoming f (AA): even steps slot q of the own cell, odd steps slot opp(q) of x - e_q
     float f[LF::Q];
 #pragma unroll
@@ -190,6 +197,15 @@ __global__ void __launch_bounds__(kThreads) bao_collide_kernel(const StepArgs a,
   const float itau = P.lks_itau, fwt = 1.0f - 0.5f * P.lks_itau;
   pass_walk<DIM>(G, [&](const PassCell& cl) {
     const unsigned c = cl.c;
+    // next plane: lanes 0..QG-1 the g lines, then the f lines, then the
+    // field rows (phi, mu, p, u)
+    const long long rn = next_plane_row<DIM>(G, cl);
+    if (rn >= 0) {
+      const int l = threadIdx.x;
+      if (l < LG::Q) prefetch_l2(group_line<LG>(gs, rn, l));
+      else if (l < LG::Q + LF::Q) prefetch_l2(group_line<LF>(fb, rn, l - LG::Q));
+      else if (l < LG::Q + LF::Q + 3 + DIM) prefetch_l2(a.work + (size_t)(l - LG::Q - LF::Q) * a.N + rn);
+    }
     float vp[LS::Q], vpr[LS::Q];
     gather<DIM, LS>(phi, cl, vp);
     gather<DIM, LS>(pf, cl, vpr);

@@ -201,6 +201,18 @@ __global__ void __launch_bounds__(kThreads) liu_collide_kernel(const StepArgs a,
   pass_walk<DIM>(G, [&](const PassCell& cl) {
     const unsigned c = cl.c;
     const int x = cl.x, y = cl.y, z = cl.z;
+    // next plane: lanes 0..QG-1 the g lines, then the f lines, then the
+    // rows of phi, lambda, phi* and phi u
+    const long long rn = next_plane_row<DIM>(G, cl);
+    if (rn >= 0) {
+      const int l = threadIdx.x;
+      if (l < LG::Q) prefetch_l2(group_line<LG>(gs, rn, l));
+      else if (l < LG::Q + LF::Q) prefetch_l2(group_line<LF>(fb, rn, l - LG::Q));
+      else if (l == LG::Q + LF::Q) prefetch_l2(W.phi + rn);
+      else if (l == LG::Q + LF::Q + 1) prefetch_l2(W.lam + rn);
+      else if (l == LG::Q + LF::Q + 2) prefetch_l2(W.phis + rn);
+      else if (l < LG::Q + LF::Q + 3 + DIM) prefetch_l2(a.phiu + (size_t)(l - LG::Q - LF::Q - 3) * a.N + rn);
+    }
     float nb[LS::Q];
 #pragma unroll
     for (int q = 0; q < LS::Q; ++q) nb[q] = W.phi[cl.nb(LS::ex(q), LS::ey(q), LS::ez(q))];

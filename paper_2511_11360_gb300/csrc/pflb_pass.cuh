@@ -84,4 +84,23 @@ __device__ __forceinline__ void pass_walk(const PassGeo<DIM>& G, Fn&& fn) {
   }
 }
 
+// L2 prefetch hint for the 128-byte line holding *p (no fault, no data).
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// Row start of the warp's 32 cells in the next plane (x lane = threadIdx.x),
+// or -1 when the cell is in the last plane. The per-cell passes are bound by
+// the latency of their many dependent loads; asking L2 for the next plane's
+// rows one plane ahead overlaps it with the current cell.
+template <int DIM>
+__device__ __forceinline__ long long next_plane_row(const PassGeo<DIM>& G, const PassCell& cl) {
+  if (DIM != 3 || cl.z + 1 >= G.nz) return -1;
+  return (long long)(cl.c - threadIdx.x) + (long long)G.nx * G.ny;
+}
+
+// Line q of the population group (32 cells, Q values each) that holds cell r.
+template <typename L>
+__device__ __forceinline__ const float* group_line(const float* pops, long long r, int q) {
+  return pops + ((size_t)(r >> 5) * L::Q + q) * 32;
+}
+
 }  // namespace pflb
