@@ -65,8 +65,8 @@ def _discrete_sigma(W, sigma):
 @pytest.mark.parametrize("fam", [O.FAKHARI2017, O.LIANG2014, O.LIANG2018],
                          ids=["fakhari2017", "liang2014", "liang2018"])
 def test_P2_laplace_law_2d(fam):
-    """Pressure jump across a 2D droplet, dp = sigma_d / R (Sec. IV, BASELINE
-    static droplet, 64^2, R = 16, xi = 4). tau = 1.5 damps the acoustic
+    """Pressure jump across a 2D droplet, dp = sigma_d / R (Sec. IV, the
+    static droplet case, 64^2, R = 16, xi = 4). tau = 1.5 damps the acoustic
     transient of the p = 0 start; p is averaged over the last 500 steps."""
     n, R, W, sig = 64, 16.0, 4.0, 1e-3
     P, phi, u = C.static_droplet_2d(nx=n, ny=n, R=R, W=W, family=fam,
