@@ -346,7 +346,7 @@ int pflb_batch_set_launch(pflb_batch* b, const pflb_batch_launch* cfg);
 int pflb_batch_get_launch(const pflb_batch* b, pflb_batch_launch* out);
 
 /* Choose the launch shape by timing candidate shapes (tile_a in {64, 128,
- * 256}, chunk in {4, 8, 16, 32}, blocks_per_sm in {all that fit, half})
+ * 256}, chunk in {8, 16, 32, 64}, blocks_per_sm in {all that fit, half})
  * over steps_per_trial steps each (>= 1), then restore every domain's state
  * and observables bit for bit, so tuning does not advance the batch.
  * cache_path (may be NULL): a text file keyed by the device and the batch's

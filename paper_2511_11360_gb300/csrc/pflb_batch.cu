@@ -1,6 +1,7 @@
 // C ABI of the batched step (declared in include/pflb.h): many 2D domains
 // advanced by one persistent launch per time level, optional CUDA-graph
 // replay, and an autotuner of the launch shape.
+#include <algorithm>
 #include <cinttypes>
 #include <cstdarg>
 #include <cstdio>
@@ -102,6 +103,12 @@ int build_layout(pflb_batch* b) {
       for (long long s = 0; s < h->N; s += kGammaEntryCells)
         gent.push_back(BatchGammaEntry{i, (int)s, (int)(s + kGammaEntryCells < h->N ? s + kGammaEntryCells : h->N), 0});
   }
+  // Tiles of one family together: resident blocks then run the same branch
+  // of the kernel's family dispatch (one family's code in the instruction
+  // cache at a time). The order of tiles within a step does not change the
+  // state.
+  std::stable_sort(tiles.begin(), tiles.end(),
+                   [](const BatchTile& x, const BatchTile& y) { return x.fam < y.fam; });
   int rc = upload(b, &b->d_tiles, tiles);
   if (rc) return rc;
   if ((rc = upload(b, &b->d_gent, gent))) return rc;
@@ -552,7 +559,7 @@ int pflb_batch_autotune(pflb_batch* b, int32_t steps_per_trial, const char* cach
   const pflb_batch_launch keep = b->cfg;
   double best_ms = -1.0;
   static const int tas[3] = {64, 128, 256};
-  static const int chunks[4] = {4, 8, 16, 32};
+  static const int chunks[4] = {8, 16, 32, 64};
   for (int ta : tas) {
     const int maxb = batch_max_blocks_per_sm(ta);
     const int bpss[2] = {0, maxb / 2};

@@ -123,7 +123,7 @@ def test_autotune_restores_state_and_uses_cache(tmp_path):
     before = states(b)
     cache = str(tmp_path / "batch_tuning.txt")
     cfg = b.autotune(steps_per_trial=1, cache_path=cache)
-    assert cfg["tile_a"] in (64, 128, 256) and cfg["chunk"] in (4, 8, 16, 32)
+    assert cfg["tile_a"] in (64, 128, 256) and cfg["chunk"] in (8, 16, 32, 64)
     assert cfg["ms_per_step"] > 0 and cfg["from_cache"] == 0
     assert b.launch()["tile_a"] == cfg["tile_a"]
     assert all(b.domain(i).step_count == 3 for i in range(b.n))
