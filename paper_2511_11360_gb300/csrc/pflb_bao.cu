@@ -62,14 +62,14 @@ __global__ void __launch_bounds__(kThreads) bao_mu_kernel(const StepArgs a, Pass
   });
 }
 
-// grad mu, lap mu and div(M grad mu) = M lap mu + grad M . grad mu (Reading R21)
+// grad mu, lap mu and div(M grad mu) = M lap mu + grad M . grad mu (Reading R21),
+// from phi at the stencil neighbours (vp, already gathered by the caller)
 template <int DIM>
-__device__ __forceinline__ void bao_flux(const DevParams& P, const float* phi, const float* mu, const PassCell& cl,
-                                         float phic, float (&gmu)[DIM], float& divJ) {
+__device__ __forceinline__ void bao_flux(const DevParams& P, const float (&vp)[Lattices<DIM>::S::Q], const float* mu,
+                                         const PassCell& cl, float phic, float (&gmu)[DIM], float& divJ) {
   using LS = typename Lattices<DIM>::S;
-  float vm[LS::Q], vp[LS::Q];
+  float vm[LS::Q];
   gather<DIM, LS>(mu, cl, vm);
-  gather<DIM, LS>(phi, cl, vp);
   float vM[LS::Q];
 #pragma unroll
   for (int q = 0; q < LS::Q; ++q) vM[q] = bao_M(P, vp[q]);
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kThreads) bao_macro_kernel(const StepArgs a, P
     gather<DIM, LS>(phi, cl, vp);
     const float pc = vp[0];
     float gp[DIM], gmu[DIM], divJ;
-    bao_flux<DIM>(P, phi, mu, cl, pc, gmu, divJ);
+    bao_flux<DIM>(P, vp, mu, cl, pc, gmu, divJ);
     const float rho = P.rhoL + P.drho_dphi * (pc - P.phiL);
     const float muc = mu[c];
     float u[DIM], Fs[DIM], Fb[DIM];
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kThreads) bao_collide_kernel(const StepArgs a,
     gather<DIM, LS>(pf, cl, vpr);
     const float pc = vp[0], p = vpr[0], muc = mu[c];
     float gmu[DIM], divJ;
-    bao_flux<DIM>(P, phi, mu, cl, pc, gmu, divJ);
+    bao_flux<DIM>(P, vp, mu, cl, pc, gmu, divJ);
     const float rho = P.rhoL + P.drho_dphi * (pc - P.phiL);
     const float nu = viscosity(P, pc, rho);
     const float A_lks = (1.0f / itp) - 0.5f - bao_M(P, pc) * 3.0f / P.eta;   // Eq. (bao_Mphi)
