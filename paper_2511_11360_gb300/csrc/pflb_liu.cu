@@ -96,9 +96,10 @@ __global__ void __launch_bounds__(kThreads) liu_reinit_kernel(const float* __res
     float pzm = psi_in[xc + yc + nxy * (unsigned)(z0 == 0 ? G.nz - 1 : z0 - 1)];
     float pzc = psi_in[xc + yc + nxy * (unsigned)z0];
     // U planes per round, all of their loads issued before any update (the
-    // update is cheap, so the march is bound by how many loads are in flight);
-    // planes past the run repeat its last plane and are not stored
-    constexpr int U = 4;
+    // update is cheap, so the march is bound by how many loads are in flight;
+    // at 512^3 U = 2 measured best: 8 cost occupancy); planes past the run
+    // repeat its last plane and are not stored
+    constexpr int U = 2;
     for (int z = z0; z < z1; z += U) {
       float zn[U], vxm[U], vxp[U], vym[U], vyp[U], sv[U];
 #pragma unroll
