@@ -69,6 +69,20 @@ def _traffic(n):
     return None
 
 
+def _launches_per_step(family, W):
+    """The library's kernel launches per step of a family: the fused step,
+    plus the gamma pre-pass for the nonlocal and hybrid families; the pass
+    sequences of Bao2024 (four passes) and Liu2023 (predictor, ceil(6 W)
+    reinitialisation sweeps, gamma, phi, collision)."""
+    if family in (1, 2):
+        return 2
+    if family == 5:
+        return 4
+    if family == 6:
+        return 4 + int(math.ceil(6.0 * W))
+    return 1
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -367,6 +381,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--family", default="fakhari2017",
+                    choices=["fakhari2017", "chai2018", "hu2019", "liang2014", "liang2018", "bao2024", "liu2023"],
+                    help="phase-field family of the primary leg (the headline is fakhari2017)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
@@ -399,6 +416,8 @@ def main():
     n = args.n
     count = max(1, int(round(200 * (n / 512.0) ** 3)))
     P, phi, u, centres = C.hit_droplets_3d_torch(n=n, count=count, seed=C.DEFAULT_SEED + rank)
+    family = {v: k for k, v in C.FAMILY_NAMES.items()}[args.family]
+    P = dict(P, family=family)
     cells = n ** 3
     peak, peak_kind = _peaks()
 
@@ -417,7 +436,7 @@ def main():
     value = cells * args.steps * world / t / 1e9
     ms = t / args.steps * 1e3
     achieved = bytes_lu * cells / (t / args.steps) / 1e9
-    traffic = _traffic(n) if storage == 0 else None
+    traffic = _traffic(n) if storage == 0 and family == C.FAKHARI2017 else None
 
     # ---- variants: FP16 / BF16 deviation storage
     variants = {}
@@ -439,6 +458,8 @@ def main():
             # Table III compares the families' cost on one 3D case).
             fams = {}
             for fam in (C.CHAI2018, C.HU2019, C.LIANG2014, C.LIANG2018, C.BAO2024, C.LIU2023):
+                if fam == family:
+                    continue
                 s3 = pflb.Sim(dict(P, family=fam, storage=storage, obs_capacity=4),
                               stream=torch.cuda.current_stream())
                 s3.init(phi, u)
@@ -492,15 +513,16 @@ def main():
         "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": cells, "family": "fakhari2017",
+        "config": {"workload": WORKLOAD, "cells": cells, "family": args.family,
                    "storage": args.storage, "l2": "state %.1f GB >> 126 MB L2, no flush needed" % (
                        bytes_lu * cells / 2 / 1e9),
                    "bytes_per_lu": bytes_lu, "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "step_kernel<fakhari,3D,%s>" % args.storage},
+                     "kernel": ("step_kernel<%s,3D,%s>" % (args.family, args.storage))
+                     if family not in (C.BAO2024, C.LIU2023) else "%s pass sequence (whole step)" % args.family},
         "e2e": e2e,
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * _launches_per_step(family, P["W"]),
         "clocks": ck,
         "variants": variants,
         "err_vs_oracle": "fp32: phi,u rel Linf <= 1e-5 after 1000 steps (laminar, tests/test_gpu_parity.py); "
