@@ -8,18 +8,19 @@ namespace pflb {
 
 // Tile of the single-domain step kernel: cells per block along the two fast
 // axes (ta x tb) and the resident blocks per SM its register budget is sized
-// for. Staging the next plane's populations in shared memory needs up to
-// 168 registers a thread in 3D (12 warps per SM). The 16-bit forms, bound by
-// instruction issue rather than DRAM, fit 128 registers without spills and
-// take a fourth block per SM (16 warps: 31.3 -> 32.5 GLUPS at 512^3).
+// for. The 3D Allen-Cahn tiles fit 128 registers a thread without spills and
+// run four blocks per SM (16 warps; FP32 with three f stages so that four
+// blocks fit in shared memory): 16-bit storage, bound by instruction issue,
+// went from 31.3 to 32.5 GLUPS at 512^3 against three blocks, FP32 from 24.7
+// to 25.2. Cahn-Hilliard and D3Q27 tiles need up to 168 and 220 registers.
 struct TileShape {
   int ta, tb, minb;
 };
 __host__ __device__ constexpr TileShape tile_shape(int family, int dim, int storage, int lat = 0) {
   // D3Q27 holds 27 populations (and with MRT their moments) a thread: two blocks per SM.
-  return dim == 2 ? TileShape{128, 1, 4}
+  return (void)storage, dim == 2 ? TileShape{128, 1, 4}
          : family == 3 ? TileShape{32, 6, 2}
-         : lat == 1 ? TileShape{32, 4, 2} : storage != 0 ? TileShape{32, 4, 4} : TileShape{32, 4, 3};
+         : lat == 1 ? TileShape{32, 4, 2} : TileShape{32, 4, 4};
 }
 
 struct StepArgs {

@@ -420,9 +420,12 @@ struct TileSmem {
   static constexpr int FST = COOP ? Lattices<DIM, LAT>::F::Q * TB * FROW * (int)sizeof(T) / 4
                                   : Lattices<DIM, LAT>::F::Q * NT;
   static constexpr int GST = Lattices<DIM, LAT>::G::Q * PLANE;
-  // COOP refills a stage only after the next plane's barrier, so it keeps one
-  // stage more in flight (Cahn-Hilliard tiles have no room for it).
-  static constexpr int NST = (COOP && !CH) ? 4 : 3;
+  // COOP refills a stage only after the next plane's barrier, so a fourth
+  // stage keeps one more plane in flight. The FP32 D3Q19 tiles take three
+  // stages instead, which lets a fourth block fit per SM (53 KB each; 16
+  // warps hide more latency than the extra stage: 24.7 -> 25.2 GLUPS at
+  // 512^3); Cahn-Hilliard tiles have no room for a fourth stage.
+  static constexpr int NST = (COOP && !CH && (sizeof(T) < 4 || LAT == 1)) ? 4 : 3;
   static constexpr int STAGE = STAGED ? NST * (FST + GST) : 0;
   static_assert(!COOP || (FST % 4 == 0 && GST % 4 == 0), "16-byte aligned stages");
   static constexpr size_t BYTES = (size_t)(STAGE + PHI + MU) * sizeof(float);
