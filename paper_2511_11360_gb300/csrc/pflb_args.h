@@ -12,15 +12,17 @@ namespace pflb {
 // run four blocks per SM (16 warps; FP32 with three f stages so that four
 // blocks fit in shared memory): 16-bit storage, bound by instruction issue,
 // went from 31.3 to 32.5 GLUPS at 512^3 against three blocks, FP32 from 24.7
-// to 25.2. Cahn-Hilliard and D3Q27 tiles need up to 168 and 220 registers.
+// to 25.3. D3Q27 and Cahn-Hilliard tiles run three and two blocks per SM at
+// up to 168 registers.
 struct TileShape {
   int ta, tb, minb;
 };
 __host__ __device__ constexpr TileShape tile_shape(int family, int dim, int storage, int lat = 0) {
-  // D3Q27 holds 27 populations (and with MRT their moments) a thread: two blocks per SM.
+  // D3Q27 holds 27 populations (and with MRT their moments) a thread: three
+  // blocks per SM at 168 registers (no spills).
   return (void)storage, dim == 2 ? TileShape{128, 1, 4}
          : family == 3 ? TileShape{32, 6, 2}
-         : lat == 1 ? TileShape{32, 4, 2} : TileShape{32, 4, 4};
+         : lat == 1 ? TileShape{32, 4, 3} : TileShape{32, 4, 4};
 }
 
 struct StepArgs {

@@ -421,11 +421,11 @@ struct TileSmem {
                                   : Lattices<DIM, LAT>::F::Q * NT;
   static constexpr int GST = Lattices<DIM, LAT>::G::Q * PLANE;
   // COOP refills a stage only after the next plane's barrier, so a fourth
-  // stage keeps one more plane in flight. The FP32 D3Q19 tiles take three
-  // stages instead, which lets a fourth block fit per SM (53 KB each; 16
-  // warps hide more latency than the extra stage: 24.7 -> 25.2 GLUPS at
-  // 512^3); Cahn-Hilliard tiles have no room for a fourth stage.
-  static constexpr int NST = (COOP && !CH && (sizeof(T) < 4 || LAT == 1)) ? 4 : 3;
+  // stage keeps one more plane in flight. The FP32 tiles take three stages
+  // instead, which lets one more block fit per SM (D3Q19: four blocks of 53
+  // KB, 16 warps, 24.96 -> 25.27 GLUPS at 512^3; D3Q27: three of 67 KB);
+  // Cahn-Hilliard tiles have no room for a fourth stage.
+  static constexpr int NST = (COOP && !CH && sizeof(T) < 4) ? 4 : 3;
   static constexpr int STAGE = STAGED ? NST * (FST + GST) : 0;
   static_assert(!COOP || (FST % 4 == 0 && GST % 4 == 0), "16-byte aligned stages");
   static constexpr size_t BYTES = (size_t)(STAGE + PHI + MU) * sizeof(float);
