@@ -163,13 +163,21 @@ def _barrier(world):
 
 
 def _max_over_ranks(v, world):
+    """The largest v over the ranks (the job's time is its slowest rank's)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def _job_glups(cells, steps, world, seconds):
+    """Whole-job throughput: every rank advances its own cells (weak scaling,
+    replicas), all in the slowest rank's time."""
+    return cells * steps * world / seconds / 1e9
 
 
 def time_steps(sim, steps, warmup, world):
@@ -433,7 +441,7 @@ def main():
     t = _max_over_ranks(t, world)
     obs = sim.observables()
     sim.close()
-    value = cells * args.steps * world / t / 1e9
+    value = _job_glups(cells, args.steps, world, t)
     ms = t / args.steps * 1e3
     achieved = bytes_lu * cells / (t / args.steps) / 1e9
     traffic = _traffic(n) if storage == 0 and family == C.FAKHARI2017 else None
