@@ -1,5 +1,6 @@
-// Cell walk of the multi-pass families (Bao2024, Liu2023): blocks of 32 x 8
-// threads over (x, y), each marching over a run of z planes. Coordinates are
+// Cell walk of the per-cell pass kernels (the Bao2024 and Liu2023 passes,
+// the adjoint's reverse sweep, the canonical copy): blocks of 32 x 8 threads
+// over (x, y), each marching over a run of z planes. Coordinates are
 // known from the launch, so no cell index is ever divided; the periodic
 // neighbour offsets of the x and y axes are built once per thread and those
 // of z once per plane. A warp covers 32 consecutive x of one row, i.e. one
@@ -26,8 +27,9 @@ struct PassGeo {
   }
 };
 
-// Planes per block: enough blocks for 8 per SM several times over, runs
-// long enough to keep the neighbour planes of a block in its L1.
+// Planes per block: about 32 blocks per SM over the grid (several waves of
+// resident blocks), runs of at most 32 planes, long enough that a block's
+// neighbour planes are still in its L1 when it reaches them.
 template <int DIM>
 __host__ inline PassGeo<DIM> pass_geo(int nx, int ny, int nz, int sms) {
   PassGeo<DIM> G{nx, ny, DIM == 3 ? nz : 1, 1};
@@ -84,7 +86,8 @@ __device__ __forceinline__ void pass_walk(const PassGeo<DIM>& G, Fn&& fn) {
   }
 }
 
-// L2 prefetch hint for the 128-byte line holding *p (no fault, no data).
+// L2 prefetch hint for the 128-byte line holding *p (callers pass addresses
+// inside their buffers; nothing is returned).
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
 // Row start of the warp's 32 cells in the next plane (x lane = threadIdx.x),
