@@ -293,3 +293,37 @@ def test_P7_translation_centroid_follows_flow(fam):
     off = math.hypot(c1[0] - c0[0], c1[1] - c0[1])
     assert l2 < 3e-2 and off < 0.2, (l2, off)
     assert abs(np.sum(phi1) / s0 - 1) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Plane Couette flow between moving walls (Reading R9, moving-wall branch)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("fam,tau", [(C.FAKHARI2017, 0.8), (C.FAKHARI2017, 1.3), (C.LIANG2018, 0.8),
+                                     (C.LIANG2018, 1.3), (C.HU2019, 1.0)],
+                         ids=["fakhari2017-0.8", "fakhari2017-1.3", "liang2018-0.8", "liang2018-1.3", "hu2019-1.0"])
+def test_plane_couette_moving_walls_exact(fam, tau):
+    """Single phase between walls moving at u_b and u_t (halfway bounce-back
+    with the moving-wall term): the exact steady solution is the linear
+    profile u_x = u_b + (u_t - u_b)(y + 1/2)/ny, u_y = 0, uniform p, and the
+    phase-field flux sum e g = phi u. Started on it, the oracle stays on it
+    to round-off for both forms of the wall term's scale: 1 for the
+    velocity-based f (Fakhari2017, Hu2019), rho for the pressure-based f
+    (Liang2018, here rho = 2.5), phi for g (here phi = phi_H = 2). A wrong
+    sign, factor or scale in the wall term moves the wall cells by O(u_w)."""
+    ny, ub, ut = 8, -0.01, 0.03
+    P = C.params(dim=2, nx=2, ny=ny, family=fam, bc_y=2, wall_u=(ub, ut), phi_H=2.0, phi_L=0.0,
+                 rho_H=2.5, rho_L=1.0, nu_H=(tau - 0.5) / 3, nu_L=(tau - 0.5) / 3)
+    y = np.arange(ny) + 0.5
+    ux = ub + (ut - ub) * y / ny
+    phi = np.full((ny, 2), 2.0)
+    u = np.zeros((2, ny, 2))
+    u[0] = ux[:, None]
+    st = O.run(P, O.init_state(P, phi, u), 300)
+    m = O.macroscopic(P, st)
+    lg = O.lattices_of(P)[0]
+    jx = np.tensordot(lg.ef[:, 0], st.g, axes=(0, 0))
+    assert np.max(np.abs(m["u"][0] - ux[:, None])) < 1e-15
+    assert np.max(np.abs(m["u"][1])) < 1e-15
+    assert np.max(np.abs(m["phi"] - 2.0)) < 1e-14
+    assert np.max(np.abs(jx - 2.0 * ux[:, None])) < 1e-14
+    assert np.ptp(m["p"]) < 1e-15
