@@ -397,12 +397,19 @@ const char* pflb_batch_last_error(const pflb_batch* b);
  *
  * Returns PFLB_EINVAL for a NULL argument, bad sizes, phi_H == phi_L, or
  * N > PFLB_STATIC_MAX_CELLS (2^28 cells: the scratch holds one partial record
- * per 65536 cells); PFLB_ECUDA without a device or on a CUDA error. The first
- * call on a device looks up the scratch array's device address (with that
- * device current); make that first call before any stream capture. The
- * result does not depend on the previous call (every record used is written
- * before it is read), but all calls share the array: calls that overlap on
- * the GPU (different streams or host threads) race and must be serialised.
+ * per 65536 cells); PFLB_ECUDA without a device or on a CUDA error. Every
+ * call looks up the scratch array's device address on the current device
+ * (cudaGetSymbolAddress, no allocation), so a device reset or a new context
+ * leaves no stale address behind. The call copies its result to the host
+ * and synchronises the stream: it must not be called while that stream is
+ * being captured into a CUDA graph. The result does not depend on the
+ * previous call (every record used is written before it is read), but all
+ * calls share the array: calls that overlap on the GPU (different streams or
+ * host threads) race and must be serialised.
+ *
+ * The library cannot check phi's length or residence: a host pointer or a
+ * buffer shorter than N floats is read out of bounds. The Python binding
+ * refuses such buffers before the call.
  * ------------------------------------------------------------------------- */
 #define PFLB_STATIC_PARTIALS 4096
 #define PFLB_STATIC_CELLS_PER_BLOCK 65536LL

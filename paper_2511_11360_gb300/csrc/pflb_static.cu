@@ -14,9 +14,9 @@
 // Every record used is written in full before it is read, so nothing needs
 // clearing between calls, and the result is deterministic. The array keeps
 // the last call's contents. Calls that overlap on the GPU (other streams,
-// other host threads) share the array and race: serialise them.
-#include <mutex>
-
+// other host threads) share the array and race: serialise them. The call
+// copies its result to the host and synchronises the stream, so it cannot
+// be used while the stream is being captured into a CUDA graph.
 #include "../../include/pflb.h"
 #include "pflb_common.cuh"
 
@@ -97,22 +97,17 @@ __global__ void phase_sums_pass2(int nblocks, Partial* scratch) {
   scratch[kPartials] = r;
 }
 
-// Device address of g_scratch, looked up once per device with that device
-// current (the host-side name of a __device__ array is not a device address).
-std::mutex g_mu;
-Partial* g_addr[64] = {nullptr};
-
+// Device address of g_scratch on the current device. The host-side name of a
+// __device__ array is not a device address, so it is looked up with the
+// device current -- on every call: the lookup is cheap, and a cached address
+// would go stale after cudaDeviceReset or a new context.
 int scratch_address(Partial** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return PFLB_ECUDA; }
-  if (dev < 0 || dev >= 64) return PFLB_ECUDA;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (g_addr[dev] == nullptr) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess) { cudaGetLastError(); return PFLB_ECUDA; }
-    g_addr[dev] = static_cast<Partial*>(p);
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || p == nullptr) {
+    cudaGetLastError();
+    return PFLB_ECUDA;
   }
-  *out = g_addr[dev];
+  *out = static_cast<Partial*>(p);
   return PFLB_OK;
 }
 

@@ -421,9 +421,35 @@ def lattice(dim, which):
 STATIC_MAX_CELLS = 4096 * 65536
 
 
+def _static_cells(params):
+    d = int(params["dim"])
+    return int(params["nx"]) * int(params["ny"]) * (int(params.get("nz", 1)) if d == 3 else 1)
+
+
+def check_static_phi(params, phi):
+    """Refuse, before any library call, a phi buffer the allocation-free entry
+    point would read out of bounds: it reads N = nx*ny*nz float32 values
+    straight from device memory, and the C side cannot see a buffer's type,
+    device or length. phi must be a contiguous float32 CUDA tensor with at
+    least N elements."""
+    if not hasattr(phi, "data_ptr") or not hasattr(phi, "is_cuda") or not hasattr(phi, "numel"):
+        raise ValueError("phi must be a torch CUDA tensor (got %r)" % type(phi).__name__)
+    if str(phi.dtype) != "torch.float32":
+        raise ValueError("phi must be float32 (got %s)" % phi.dtype)
+    if not phi.is_contiguous():
+        raise ValueError("phi must be contiguous")
+    n = _static_cells(params)
+    if phi.numel() < n:
+        raise ValueError("phi holds %d values, the field needs %d" % (phi.numel(), n))
+    if not phi.is_cuda:
+        raise ValueError("phi must live on a CUDA device")
+
+
 def phase_sums_static(params, phi, stream=None):
     """pflb_phase_sums_static: the phase-field sums of a device phi field with
-    no device allocation (for callers that cannot allocate; see pflb.h)."""
+    no device allocation (for callers that cannot allocate; see pflb.h).
+    The call synchronises the stream and must not run under stream capture."""
+    check_static_phi(params, phi)
     lib = load_library()
     p = make_params(params)
     o = Obs()
