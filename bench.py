@@ -533,8 +533,11 @@ def main():
         "gpu_launches": args.steps * _launches_per_step(family, P["W"]),
         "clocks": ck,
         "variants": variants,
-        "err_vs_oracle": "fp32: phi,u rel Linf <= 1e-5 after 1000 steps (laminar, tests/test_gpu_parity.py); "
-                         "one step at sampled 512^3 cells <= 2e-6 of max|population| (tests/test_gpu_fullsize.py)",
+        "err_vs_oracle": "fp32 laminar cases, 1000 steps: phi,u rel Linf within 1e-5, or within 3x the "
+                         "deviation of the same equations run in float32 by the oracle where that FP32 floor "
+                         "is higher (the parity tests print which cases took the widened bound, and its "
+                         "value); one step at 53 sampled 512^3 cells within 2e-6 of max|population| "
+                         "(tests/test_gpu_fullsize.py)",
         "obs_after": {"sum_phi": obs["sum_phi"], "vol_count": obs["vol_count"], "ke": obs["ke"]},
         "cpu_baseline": cpu,
     }

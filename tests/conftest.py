@@ -8,3 +8,27 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device (GB300) and the built CUDA library")
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    """Print every bound the parity checks applied (tests/gpu_common.RECORD),
+    and write them as JSON to $PFLB_PARITY_RECORD when that is set."""
+    mod = sys.modules.get("gpu_common")
+    rec = getattr(mod, "RECORD", None) if mod is not None else None
+    if not rec:
+        return
+    tr = terminalreporter
+    tr.section("parity record (%d checks, %d with a bound widened to the FP32 floor)"
+               % (len(rec), sum(1 for r in rec if r.get("widened"))))
+    for r in rec:
+        if r["kind"] == "fields":
+            tr.write_line("%-70s phi %.2e / %.1e  u %.2e / %.1e%s" % (
+                r["case"][:70], r["e_phi"], r["bound_phi"], r["e_u"], r["bound_u"],
+                "  widened (fp32 floor phi %.1e u %.1e)" % (r["floor_phi"], r["floor_u"]) if r["widened"] else ""))
+        else:
+            tr.write_line("%-70s %s" % (r["case"][:70], {k: v for k, v in r.items() if k not in ("case",)}))
+    path = os.environ.get("PFLB_PARITY_RECORD")
+    if path:
+        import json
+        with open(path, "w") as fh:
+            json.dump(rec, fh, indent=1)

@@ -1,6 +1,8 @@
 """Shared helpers of the GPU parity tests (CUDA path through the C ABI vs the
 FP64 oracle on identical seeded inputs)."""
 
+import os
+
 import numpy as np
 import pytest
 
@@ -57,13 +59,33 @@ def fp32_oracle_response(P, phi, u, nsteps, st64=None):
             float(np.max(np.abs(mb["u"].astype(np.float64) - ma["u"]))))
 
 
+# Every bound a parity check applied, in the order the checks ran: one dict
+# per call (case, steps, errors, bounds, whether the bound was widened to the
+# FP32 floor, and that floor). tests/conftest.py prints the list at the end
+# of the session and writes it as JSON to $PFLB_PARITY_RECORD when set.
+RECORD = []
+
+
+def _case_name():
+    name = os.environ.get("PYTEST_CURRENT_TEST", "?")
+    return name.split(" ")[0].split("::", 1)[-1]
+
+
+def record(kind, **kw):
+    d = dict(case=_case_name(), kind=kind)
+    d.update(kw)
+    RECORD.append(d)
+    return d
+
+
 def check_parity(sim, P, phi, u, nsteps, tol=1e-5, st=None, u_ref=None):
     """GPU fields after nsteps vs the FP64 oracle from the same inputs:
     within tol, or, where the model's FP32 floor is above tol, within 3x the
     deviation of the FP32-evaluated oracle (fp32_oracle_response), measured
     here. u is measured against max|u_oracle|, or against u_ref where given
     (a flow at rest whose only velocity is the spurious current uses the
-    capillary velocity sigma/(rho nu), Reading R15).
+    capillary velocity sigma/(rho nu), Reading R15). Every call appends its
+    errors, bounds and (when measured) the FP32 floor to RECORD.
     Returns (e_phi, e_u, bound_phi, bound_u)."""
     gphi, gu, _ = sim.fields()
     if st is None:
@@ -75,11 +97,15 @@ def check_parity(sim, P, phi, u, nsteps, tol=1e-5, st=None, u_ref=None):
     else:
         e_u = float(np.max(np.abs(np.asarray(gu, np.float64) - m["u"]))) / u_ref
     b_phi = b_u = tol
+    r_phi = r_u = None
     if e_phi > tol or e_u > tol:
         r_phi, r_u, r_uabs = fp32_oracle_response(P, phi, u, nsteps, st64=st)
         if u_ref is not None:
             r_u = r_uabs / u_ref
         b_phi, b_u = max(tol, 3 * r_phi), max(tol, 3 * r_u)
+    record("fields", steps=int(nsteps), tol=tol, e_phi=e_phi, e_u=e_u, bound_phi=b_phi, bound_u=b_u,
+           widened=bool(b_phi > tol or b_u > tol), floor_phi=r_phi, floor_u=r_u,
+           passed=bool(e_phi <= b_phi and e_u <= b_u))
     assert e_phi <= b_phi, ("phi", e_phi, b_phi)
     assert e_u <= b_u, ("u", e_u, b_u)
     return e_phi, e_u, b_phi, b_u
