@@ -43,7 +43,8 @@ WORKLOAD = ("3D droplet-laden forced HIT 512^3 periodic, D3Q19+D3Q7, 200 droplet
             "We=5, density ratio 1, linear forcing, conservative Allen-Cahn (Fakhari2017)")
 METRIC = "coupled GLUPS (512^3 D3Q19+D3Q7 fused PF-LB step)"
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "step_kernel_traffic_fakhari3d_fp32.txt")
-KERNEL_SOURCES = ["pflb_step.cuh", "pflb_common.cuh", "pflb_symsum.cuh", "pflb_args.h", "pflb_fam_fakhari.cu"]
+KERNEL_SOURCES = ["pflb_step.cuh", "pflb_common.cuh", "pflb_symsum.cuh", "pflb_args.h", "pflb_tma.cuh",
+                  "pflb_fam_fakhari.cu"]
 
 
 def _traffic(n):
@@ -273,6 +274,68 @@ def batched_variant(steps, warmup, peak, count=512):
                              "sampled domains vs FP64 oracle as the 2D fp32 path (tests/test_gpu_batch.py)"}
 
 
+def weber_series_variant(n=512, steps=2000, spin=1000, wes=(1.0, 5.0, 20.0), every=200):
+    """The droplet-laden turbulence workload at three Weber numbers, FP32 and
+    FP16 / BF16 deviation storage: the single-phase flow is first spun up
+    through the library (FP32, the solenoidal field with the workload's linear
+    forcing, no droplets), then the 200 droplets are inserted and each run
+    records the droplet volume (count of phi > phi_0, Sec. IV A) and kinetic
+    energy at every step. Reports V(t)/V(0) and KE(t)/KE(0) every `every`
+    steps for FP32, and the largest deviation of the 16-bit runs from FP32:
+    |V16 - V32| / V32(0) and |KE16 - KE32| / KE32(t)."""
+    import numpy as np
+    import torch
+    from paper_2511_11360_gb300 import cases as C
+    from paper_2511_11360_gb300 import pflb
+    stream = torch.cuda.current_stream()
+    P0, phi, u, _ = C.hit_droplets_3d_torch(n=n, count=max(1, int(round(200 * (n / 512.0) ** 3))),
+                                            seed=C.DEFAULT_SEED)
+    s0 = pflb.Sim(dict(P0, obs_capacity=4), stream=stream)
+    s0.init(torch.zeros_like(phi), u)
+    s0.step(spin)
+    s0.fields(u=u)
+    ke = s0.observables()["ke"]
+    s0.close()
+    u_prime = math.sqrt(2.0 * ke / (3.0 * n ** 3))
+    out = {"spin_up_steps": spin, "u_prime_after_spin_up": u_prime, "steps": steps,
+           "sigma": "rho u'^2 (2R) / We with u' after the spin-up", "by_We": {}}
+    for We in wes:
+        P = dict(P0, sigma=u_prime ** 2 * 2.0 * 16.0 / We)   # droplets of R = 16
+        series = {}
+        for name, st in (("fp32", 0), ("fp16", 1), ("bf16", 2)):
+            sim = pflb.Sim(dict(P, storage=st, obs_capacity=steps + 8), stream=stream)
+            sim.init(phi, u)
+            done, status = 0, "stable"
+            while done < steps:
+                k = min(500, steps - done)
+                sim.step(k)
+                done += k
+                try:
+                    sim.sync()
+                except pflb.PflbError as ex:
+                    status = "unstable by step %d (%s)" % (done, ex)
+                    break
+            h = sim.history(done)
+            sim.close()
+            ok = [o["status"] == 0 for o in h]
+            n_ok = ok.index(False) if False in ok else len(ok)   # steps before the first flagged one
+            series[name] = (np.array([o["vol_count"] for o in h[:n_ok]], np.float64),
+                            np.array([o["ke"] for o in h[:n_ok]], np.float64), status)
+        v32, k32, s32 = series["fp32"]
+        row = {"fp32_V_over_V0": (v32[::every] / v32[0]).round(5).tolist(),
+               "fp32_KE_over_KE0": (k32[::every] / k32[0]).round(5).tolist(), "fp32_status": s32}
+        for name in ("fp16", "bf16"):
+            v, k, st = series[name]
+            m = min(len(v), len(v32))
+            row[name + "_status"] = st
+            row[name + "_steps_compared"] = m
+            if m:
+                row[name + "_max_dV_vs_fp32"] = float(np.max(np.abs(v[:m] - v32[:m])) / v32[0])
+                row[name + "_max_dKE_vs_fp32"] = float(np.max(np.abs(k[:m] - k32[:m]) / k32[:m]))
+        out["by_We"]["%g" % We] = row
+    return out
+
+
 def adjoint_variant(n=128, nsteps=2000):
     """Adjoint of the 3D droplet in a Taylor-Green vortex (n^3 periodic, R = 24,
     W = 4, u0 = 0.02, M = 0.1, sigma = 1e-3, tau = 0.8): forward sweep with
@@ -326,55 +389,80 @@ def adjoint_variant(n=128, nsteps=2000):
             "dJ_dsigma_central_difference_fp32": fd, "max_abs_dJ_du0": float(du0.abs().max())}
 
 
-def cpu_baseline(seconds_target=15.0):
-    """The FP64 oracle, unmodified, on a bounded sample of the workload: a
-    periodic 64^3 box of the same recipe (2 droplets of R = 16, W = 4,
-    solenoidal velocity), as many steps as fit the target time."""
-    import numpy as np
+_BARRIER = None
+
+
+def _oracle_worker_init(barrier):
+    global _BARRIER
+    _BARRIER = barrier
+
+
+def _oracle_sample_run(n, warmup, steps, seed):
+    """One host core: the FP64 oracle, unmodified, on a periodic n^3 box of
+    the workload's recipe (2 droplets of R = 16, W = 4, solenoidal u);
+    returns the seconds of its `steps` timed steps. Workers start their timed
+    loops together at a barrier, so the loops overlap."""
     import oracle as O
     from paper_2511_11360_gb300 import cases as C
-    n = 64
-    P, phi, u, _ = C.hit_droplets_3d(n=n, count=2, R=16.0, W=4.0, We=5.0, seed=C.DEFAULT_SEED)
+    P, phi, u, _ = C.hit_droplets_3d(n=n, count=2, R=16.0, W=4.0, We=5.0, seed=seed)
     st = O.init_state(P, phi, u)
-    t0 = time.perf_counter()
-    steps = 0
-    while True:
+    for _ in range(warmup):
         st = O.step(P, st)
-        steps += 1
-        if time.perf_counter() - t0 > seconds_target or steps >= 50:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": n ** 3 * steps / dt / 1e9, "unit": "GLUPS", "cores": 1, "kind": "oracle",
-            "sample": "%d steps of a 64^3 periodic box of the same recipe (2 droplets R=16, W=4, "
-                      "solenoidal u), numpy float64, single thread; %.1f s" % (steps, dt)}
+    if _BARRIER is not None:
+        _BARRIER.wait()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st = O.step(P, st)
+    return time.perf_counter() - t0
+
+
+def oracle_on_host_cores(n, warmup, steps, cores=None):
+    """The oracle on every host core at once (one process and one n^3 sample
+    per core, spawned), aggregate cells x steps / s over the slowest core's
+    timed loop. Returns (GLUPS, cores, seconds)."""
+    import concurrent.futures as cf
+    import multiprocessing
+    cores = cores or os.cpu_count() or 1
+    ctx = multiprocessing.get_context("spawn")
+    barrier = ctx.Barrier(cores)
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=ctx, initializer=_oracle_worker_init,
+                                initargs=(barrier,)) as ex:
+        times = list(ex.map(_oracle_sample_run, [n] * cores, [warmup] * cores, [steps] * cores,
+                            [20251114 + k for k in range(cores)]))
+    t = max(times)
+    return cores * n ** 3 * steps / t / 1e9, cores, t
+
+
+def cpu_baseline(steps=16):
+    """The FP64 oracle, unmodified, on bounded samples of the workload: a
+    periodic 64^3 box of the same recipe (2 droplets of R = 16, W = 4,
+    solenoidal velocity) per host core, all cores at once (numpy runs each
+    oracle step on one thread)."""
+    n = 64
+    value, cores, t = oracle_on_host_cores(n, 1, steps)
+    return {"value": value, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+            "sample": "%d cores, each %d oracle steps of its own 64^3 periodic box of the same recipe (2 droplets "
+                      "R=16, W=4, solenoidal u), numpy float64, one thread per core; slowest core %.1f s"
+                      % (cores, steps, t)}
 
 
 def reference_main(args):
-    """The FP64 oracle as it stands, timed on the host cores: each step is one
-    oracle step of a periodic 64^3 sample of the same recipe."""
+    """The FP64 oracle as it stands, on all host cores: each step is one
+    oracle step of a periodic 64^3 sample of the same recipe on every core at
+    once (one sample per core)."""
     rank, world, local = _dist()
     if rank != 0:
         return 0
-    import oracle as O
-    from paper_2511_11360_gb300 import cases as C
     n = 64
-    P, phi, u, _ = C.hit_droplets_3d(n=n, count=2, R=16.0, W=4.0, We=5.0, seed=C.DEFAULT_SEED)
-    st = O.init_state(P, phi, u)
-    for _ in range(args.warmup):
-        st = O.step(P, st)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        st = O.step(P, st)
-    dt = time.perf_counter() - t0
-    value = n ** 3 * args.steps / dt / 1e9
-    sample = ("%d oracle steps of a 64^3 periodic box of the same recipe (2 droplets R=16, W=4, "
-              "solenoidal u), numpy float64, single thread" % args.steps)
+    value, cores, dt = oracle_on_host_cores(n, args.warmup, args.steps)
+    sample = ("%d cores, each %d oracle steps of its own 64^3 periodic box of the same recipe (2 droplets R=16, "
+              "W=4, solenoidal u), numpy float64, one thread per core" % (cores, args.steps))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / max(args.steps, 1) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + " (bounded 64^3 sample on host cores)"},
-            "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+            "config": {"workload": WORKLOAD + " (bounded 64^3 samples on host cores)"},
+            "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -392,11 +480,14 @@ def main():
     ap.add_argument("--family", default="fakhari2017",
                     choices=["fakhari2017", "chai2018", "hu2019", "liang2014", "liang2018", "bao2024", "liu2023"],
                     help="phase-field family of the primary leg (the headline is fakhari2017)")
+    ap.add_argument("--staging", type=int, default=1, choices=[0, 1],
+                    help="1: TMA staging of the populations (default, where the geometry allows); 0: cp.async")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-families", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-weber", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -433,6 +524,8 @@ def main():
     storage = pflb.STORAGE[args.storage]
     sim = pflb.Sim(dict(P, storage=storage, obs_capacity=4), stream=torch.cuda.current_stream())
     sim.init(phi, u)
+    sim.set_staging(args.staging)
+    staging = "tma" if sim.staging == 1 else "cp.async"
     bytes_lu = sim.bytes_per_update()
     clocks = Clocks(local)
     clocks.start()
@@ -449,6 +542,19 @@ def main():
     # ---- variants: FP16 / BF16 deviation storage
     variants = {}
     if not args.no_variants:
+        # the same step with the other staging of the populations (TMA bulk
+        # tensor copies or per-thread cp.async), identical results
+        s1 = pflb.Sim(dict(P, storage=storage, obs_capacity=4), stream=torch.cuda.current_stream())
+        s1.init(phi, u)
+        s1.set_staging(1 - args.staging)
+        other = "tma" if s1.staging == 1 else "cp.async"
+        if other != staging:
+            t1 = _max_over_ranks(time_steps(s1, args.steps, args.warmup, world), world)
+            variants["%s_%s_staging" % (args.storage, other.replace(".", "_"))] = {
+                "value": cells * args.steps * world / t1 / 1e9, "unit": "GLUPS", "bytes_per_lu": bytes_lu,
+                "roofline_frac": bytes_lu * cells / (t1 / args.steps) / 1e9 / peak,
+                "ms_per_step": t1 / args.steps * 1e3}
+        s1.close()
         for name, st in (("fp16_storage", 1), ("bf16_storage", 2)):
             if st == storage:
                 continue
@@ -492,6 +598,8 @@ def main():
                 "roofline_frac": b4 * cells / (t4 / args.steps) / 1e9 / peak,
                 "ms_per_step": t4 / args.steps * 1e3, "time_vs_d3q19_bgk": t4 / t,
                 "collision": "MRT, raw moments, s_bulk = s_ho = 1"}
+        if not args.no_weber:
+            variants["weber_series_%d" % n] = weber_series_variant(n=n)
         if not args.no_batched:
             variants["batched_2d_shear_512"] = batched_variant(args.steps, args.warmup, peak)
         if not args.no_adjoint:
@@ -522,7 +630,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "cells": cells, "family": args.family,
-                   "storage": args.storage, "l2": "state %.1f GB >> 126 MB L2, no flush needed" % (
+                   "storage": args.storage, "staging": staging,
+                   "l2": "state %.1f GB >> 126 MB L2, no flush needed" % (
                        bytes_lu * cells / 2 / 1e9),
                    "bytes_per_lu": bytes_lu, "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

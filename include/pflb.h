@@ -140,7 +140,7 @@ typedef struct pflb_obs {
   double ke;            /* sum 1/2 rho |u|^2 */
   double phi_max, phi_min;
   double centroid[3];   /* sum x c / sum c with c = (phi - phi_L)/(phi_H - phi_L) */
-  int32_t status;       /* PFLB_OK or PFLB_EUNSTABLE */
+  int32_t status;       /* PFLB_OK, PFLB_EUNSTABLE or PFLB_ETIMEOUT */
   int32_t pad;
 } pflb_obs;
 
@@ -171,7 +171,8 @@ int pflb_init(pflb_handle* h, const float* phi0, const float* u0);
 int pflb_step(pflb_handle* h, int64_t nsteps);
 
 /* Wait for the handle's stream; returns PFLB_EUNSTABLE if any step flagged
- * an instability. */
+ * an instability, PFLB_ETIMEOUT if a step's staging copies did not complete
+ * within the kernel's bounded wait (the step's results are then invalid). */
 int pflb_sync(pflb_handle* h);
 
 /* Observables of the current state (time level pflb_step_count). Runs one
@@ -211,6 +212,22 @@ double pflb_bytes_per_update(const pflb_handle* h);
 /* Launch shape of the fused step: cells per block along the marching axis
  * (z in 3D, y in 2D), 0 = library default. */
 int pflb_set_chunk(pflb_handle* h, int32_t chunk);
+
+/* How the fused 3D step stages each plane's populations in shared memory.
+ * mode 1 (the default): tensor-memory-accelerator bulk copies of boxes of
+ * the population arrays (a 5-D view: lane, slot, 32-cell x-block, y, z),
+ * completed on shared-memory barriers whose waits are bounded -- used where
+ * the domain is 3D, nx is a multiple of 32, ny a multiple of the tile's rows
+ * (4) and at least 8, and the family is Fakhari2017, Chai2018, Hu2019 or
+ * Liang2018; elsewhere mode 1 falls back to mode 0. mode 0: per-thread
+ * cp.async copies. Both compute bit-identical results (Sec. II B and the
+ * streaming of this header's conventions are unchanged). PFLB_EINVAL for
+ * another mode. */
+int pflb_set_staging(pflb_handle* h, int32_t mode);
+
+/* 1 if the next step of h uses TMA staging, 0 if it uses cp.async staging,
+ * PFLB_EINVAL for a NULL handle. */
+int pflb_get_staging(const pflb_handle* h);
 
 /* Velocity set of a lattice in canonical order. which: 0 = phase field (g),
  * 1 = hydrodynamics (f: D2Q9 / D3Q19), 2 = the D3Q27 hydrodynamic lattice

@@ -12,6 +12,7 @@ the field layout (ny, nx) or (nz, ny, nx) (x fastest) and vectors (d, *field).
 """
 
 import math
+import os
 
 import numpy as np
 
@@ -211,10 +212,19 @@ def place_droplets(n, count, R, W, seed=DEFAULT_SEED, max_tries=200000):
 
 def droplet_field(n, centres, R, W, dtype=np.float64):
     """phi of heavy droplets (Eq. init-phi-droplet-3D profile per droplet) in a
-    periodic cube; each droplet is written in a box of half-width R + 5W and
-    combined by maximum (droplets are separated by at least 4W)."""
+    periodic cube; each droplet is written in a box of half-width R + 5W (the
+    whole cube, by minimum-image distance, where that box would wrap onto
+    itself) and combined by maximum (droplets are separated by at least 4W)."""
     phi = np.zeros((n, n, n), dtype=dtype)
     h = int(math.ceil(R + 5 * W))
+    if 2 * h + 1 > n:
+        # the box would wrap onto itself: minimum-image distances over the whole cube
+        ax = np.arange(n, dtype=np.float64) + 0.5
+        for c in centres:
+            d = [((ax - c[k] + 0.5 * n) % n) - 0.5 * n for k in range(3)]
+            r = np.sqrt(d[2][:, None, None] ** 2 + d[1][None, :, None] ** 2 + d[0][None, None, :] ** 2)
+            phi = np.maximum(phi, _tanh_profile(R - r, W).astype(dtype))
+        return phi
     off = np.arange(-h, h + 1)
     for c in centres:
         ic = np.floor(c).astype(int)
@@ -359,6 +369,14 @@ def droplet_field_torch(n, centres, R, W, device="cuda"):
     import torch
     phi = torch.zeros((n, n, n), device=device, dtype=torch.float32)
     h = int(math.ceil(R + 5 * W))
+    if 2 * h + 1 > n:
+        # the box would wrap onto itself: minimum-image distances over the whole cube
+        ax = torch.arange(n, device=device, dtype=torch.float64) + 0.5
+        for c in centres:
+            d = [((ax - float(c[k]) + 0.5 * n) % n) - 0.5 * n for k in range(3)]
+            r = torch.sqrt(d[2][:, None, None] ** 2 + d[1][None, :, None] ** 2 + d[0][None, None, :] ** 2)
+            phi = torch.maximum(phi, (0.5 + 0.5 * torch.tanh(2.0 * (R - r) / W)).to(torch.float32))
+        return phi
     off = torch.arange(-h, h + 1, device=device)
     for c in centres:
         ic = [int(math.floor(v)) for v in c]
@@ -387,3 +405,88 @@ def hit_droplets_3d_torch(n=512, count=200, R=16.0, W=4.0, We=5.0, u_rms=0.04, n
                nu_H=nu, nu_L=nu, sigma=sigma, W=W, M=M, lundgren_A=lundgren_A)
     P.update(kw)
     return P, phi, u, centres
+
+
+# --------------------------------------------------------------------------
+# Spun-up single-phase turbulence (the state droplets are inserted into)
+# --------------------------------------------------------------------------
+def spun_up_turbulence(n, nu=0.02, u_rms=0.04, k0=4.0, steps=600, dt=1.0, seed=DEFAULT_SEED, nmodes=48):
+    """Statistically stationary forced isotropic turbulence on an n^3
+    periodic box (lattice units, dx = 1), the single-phase flow the 3D study
+    of Sec. IV inserts its droplets into.
+
+    Input generation only, by a different method from the lattice Boltzmann
+    step it feeds: a pseudo-spectral solution of the incompressible
+    Navier-Stokes equations in rotational form (Fourier collocation, 2/3
+    dealiasing, Heun's second-order time step), from the random solenoidal
+    field of solenoidal_field(), driven by linear forcing A u whose
+    coefficient is set every step to the rate that holds the kinetic energy
+    constant, A = eps / (2 k) = nu <|omega|^2> / <|u|^2>.
+
+    Returns (u, stats): u is (3, n, n, n) float64 in the field layout
+    (z, y, x), component 0 = x; stats holds u' (rms per component), eps, the
+    Taylor microscale lambda = sqrt(15 nu u'^2 / eps), Re_lambda = u' lambda
+    / nu, the Kolmogorov scale eta and the mean A over the last quarter of the
+    steps (the constant linear-forcing coefficient that keeps this flow
+    stationary)."""
+    u0 = solenoidal_field((n, n, n), k0=k0, u_rms=u_rms, nmodes=nmodes, seed=seed)
+    f = 2.0 * math.pi * np.fft.fftfreq(n)
+    fr = 2.0 * math.pi * np.fft.rfftfreq(n)
+    kz, ky, kx = f[:, None, None], f[None, :, None], fr[None, None, :]
+    K = (kx, ky, kz)
+    k2 = kx * kx + ky * ky + kz * kz
+    k2s = np.where(k2 == 0.0, 1.0, k2)
+    m = np.fft.fftfreq(n) * n
+    mr = np.fft.rfftfreq(n) * n
+    cut = n / 3.0
+    mask = ((np.abs(m)[:, None, None] < cut) & (np.abs(m)[None, :, None] < cut)
+            & (np.abs(mr)[None, None, :] < cut)).astype(np.float64)
+    ax = (0, 1, 2)
+    try:
+        import scipy.fft as sfft
+        workers = os.cpu_count() or 1
+
+        def fwd(a):
+            return sfft.rfftn(a, axes=ax, workers=workers)
+
+        def inv(a):
+            return sfft.irfftn(a, s=(n, n, n), axes=ax, workers=workers)
+    except ImportError:
+        def fwd(a):
+            return np.fft.rfftn(a, axes=ax)
+
+        def inv(a):
+            return np.fft.irfftn(a, s=(n, n, n), axes=ax)
+
+    def project(vh):
+        kd = (K[0] * vh[0] + K[1] * vh[1] + K[2] * vh[2]) / k2s
+        return np.stack([vh[i] - K[i] * kd for i in range(3)])
+
+    def curl(vh):
+        return np.stack([1j * (K[1] * vh[2] - K[2] * vh[1]),
+                         1j * (K[2] * vh[0] - K[0] * vh[2]),
+                         1j * (K[0] * vh[1] - K[1] * vh[0])])
+
+    def rhs(vh):
+        v = np.stack([inv(vh[i]) for i in range(3)])
+        w = np.stack([inv(c) for c in curl(vh)])
+        A = nu * float(np.mean(np.sum(w * w, axis=0))) / float(np.mean(np.sum(v * v, axis=0)))
+        nl = np.stack([v[1] * w[2] - v[2] * w[1], v[2] * w[0] - v[0] * w[2], v[0] * w[1] - v[1] * w[0]])
+        nh = project(np.stack([fwd(nl[i]) for i in range(3)]) * mask)
+        return nh - nu * k2 * vh + A * vh, A
+
+    uh = project(np.stack([fwd(u0[i]) for i in range(3)]) * mask)
+    As = []
+    for _ in range(steps):
+        r1, a1 = rhs(uh)
+        r2, _ = rhs(uh + dt * r1)
+        uh = uh + 0.5 * dt * (r1 + r2)
+        As.append(a1)
+    u = np.stack([inv(uh[i]) for i in range(3)])
+    w = np.stack([inv(c) for c in curl(uh)])
+    up = math.sqrt(float(np.mean(np.sum(u * u, axis=0))) / 3.0)
+    eps = nu * float(np.mean(np.sum(w * w, axis=0)))
+    lam = math.sqrt(15.0 * nu * up * up / eps)
+    stats = dict(u_prime=up, eps=eps, taylor_lambda=lam, Re_lambda=up * lam / nu,
+                 eta=(nu ** 3 / eps) ** 0.25, A=float(np.mean(As[-max(1, steps // 4):])), steps=steps, dt=dt)
+    return u, stats

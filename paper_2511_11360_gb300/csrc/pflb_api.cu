@@ -217,7 +217,7 @@ void pflb::obs_to_host(const DevObs& d, long long step, pflb_obs* o) {
   o->phi_max = key_float(d.phi_max_key);
   o->phi_min = key_float(d.phi_min_key);
   for (int k = 0; k < 3; ++k) o->centroid[k] = d.vol_smooth != 0.0 ? d.cen[k] / d.vol_smooth : 0.0;
-  o->status = d.status ? PFLB_EUNSTABLE : PFLB_OK;
+  o->status = (d.status & kStatusTimeout) ? PFLB_ETIMEOUT : (d.status ? PFLB_EUNSTABLE : PFLB_OK);
   o->pad = 0;
 }
 
@@ -233,6 +233,8 @@ StepArgs pflb::handle_step_args(const pflb_handle* h) {
   a.parity = (int)(h->step & 1);
   a.chunk = h->chunk > 0 ? h->chunk : default_chunk(h);
   a.N = h->N;
+  a.tma = h->staging == 1 ? h->tma[h->cur] : nullptr;
+  a.seed = (unsigned)h->step;
   return a;
 }
 
@@ -348,6 +350,7 @@ int pflb_create(const pflb_params* params, void* cuda_stream, pflb_handle** out)
   if (h->family == PFLB_HAC_LIU2023 && (rc = alloc((void**)&h->work, (size_t)6 * h->N * sizeof(float)))) return rc;
   if ((rc = alloc((void**)&h->obs, (size_t)(h->obs_cap + 1) * sizeof(DevObs)))) return rc;
   if ((rc = alloc((void**)&h->gamma_acc, 6 * sizeof(double)))) return rc;
+  handle_build_tma(h);
   return PFLB_OK;
 }
 
@@ -424,9 +427,10 @@ int pflb_sync(pflb_handle* h) {
     CU(h, cudaMemcpy(o.data(), h->obs, h->obs_cap * sizeof(DevObs), cudaMemcpyDeviceToHost));
     for (long long i = 0; i < n; ++i) {
       const long long s = h->step - 1 - i;
-      if (o[s % h->obs_cap].status) {
-        return handle_fail(h, PFLB_EUNSTABLE, "step %lld produced rho <= 0 or non-finite phi/u", s);
-      }
+      const unsigned st = o[s % h->obs_cap].status;
+      if (st & kStatusTimeout)
+        return handle_fail(h, PFLB_ETIMEOUT, "step %lld: a staging copy did not complete in time", s);
+      if (st) return handle_fail(h, PFLB_EUNSTABLE, "step %lld produced rho <= 0 or non-finite phi/u", s);
     }
   }
   return h->status;
@@ -442,7 +446,8 @@ int pflb_observables(pflb_handle* h, pflb_obs* out) {
   CU(h, cudaMemcpyAsync(&d, h->obs + h->obs_cap, sizeof(DevObs), cudaMemcpyDeviceToHost, h->stream));
   CU(h, cudaStreamSynchronize(h->stream));
   obs_to_host(d, h->step, out);
-  if (out->status != PFLB_OK) handle_fail(h, PFLB_EUNSTABLE, "state has rho <= 0 or non-finite phi/u");
+  if (out->status == PFLB_ETIMEOUT) handle_fail(h, PFLB_ETIMEOUT, "a staging copy did not complete in time");
+  else if (out->status != PFLB_OK) handle_fail(h, PFLB_EUNSTABLE, "state has rho <= 0 or non-finite phi/u");
   return h->status;
 }
 
@@ -594,6 +599,8 @@ int pflb_destroy(pflb_handle* h) {
   cudaFree(h->obs);
   cudaFree(h->gamma_acc);
   cudaFree(h->scratch);
+  delete h->tma[0];
+  delete h->tma[1];
   delete h;
   return PFLB_OK;
 }

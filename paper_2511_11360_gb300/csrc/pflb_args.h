@@ -3,6 +3,7 @@
 #pragma once
 
 #include "pflb_common.cuh"
+#include "pflb_tma.cuh"
 
 namespace pflb {
 
@@ -43,6 +44,8 @@ struct StepArgs {
   long long N;
   double* gamma_next;     // nonlocal/hybrid: the next step's pair (zeroed by the batched pre-pass)
   float* work;            // Bao2024: phi, mu, p, u fields ((3 + d) x N); Liu2023: 6 x N
+  const TmaMaps* tma = nullptr;  // host copy of this step's tensor maps (TMA staging), or null
+  unsigned seed = 0u;     // step counter: seeds the stochastic rounding of 16-bit stores
 };
 
 struct InitArgs {

@@ -238,12 +238,37 @@ __host__ __device__ constexpr float pow2_scale(int a) {
   return s;
 }
 
+// Stochastic rounding of the per-step 16-bit stores. Round-to-nearest of a
+// value that repeats step after step (quasi-steady regions) repeats its
+// error, and the errors add up coherently -- linearly in the step count,
+// and in the sum of phi, which the populations carry. Rounding up with
+// probability equal to the dropped fraction makes each error zero-mean and
+// independent, so they add up as a random walk. The random bits come from a
+// counter-based stream per cell and step: a 32-bit integer hash of (cell,
+// step) seeds it, a 32-bit linear congruential step advances it per store,
+// and its top bits are used. The result depends only on (cell, step), not on
+// the launch shape.
+__device__ __forceinline__ unsigned dither_seed(unsigned cell, unsigned step) {
+  unsigned x = cell * 0x9E3779B9u ^ (step * 0x85EBCA6Bu + 0x2545F491u);
+  x ^= x >> 16;
+  x *= 0x7FEB352Du;
+  x ^= x >> 15;
+  x *= 0x846CA68Bu;
+  x ^= x >> 16;
+  return x;
+}
+__device__ __forceinline__ unsigned dither_next(unsigned& s) {
+  s = s * 1664525u + 1013904223u;
+  return s;
+}
+
 template <typename T> struct Codec;
 template <> struct Codec<float> {
   __device__ __forceinline__ static float ld(const float* p) { return __ldg(p); }
   __device__ __forceinline__ static float ldc(const float* p) { return *p; }
   __device__ __forceinline__ static float dec(float x, float, float) { return x; }
   __device__ __forceinline__ static void st(float* p, float v, float, float) { *p = v; }
+  __device__ __forceinline__ static void st_sr(float* p, float v, float, float, unsigned) { *p = v; }
 };
 template <> struct Codec<__half> {
   __device__ __forceinline__ static __half ld(const __half* p) { return __ldg(p); }
@@ -252,6 +277,14 @@ template <> struct Codec<__half> {
   __device__ __forceinline__ static __half from_bits(unsigned short b) { return __ushort_as_half(b); }
   __device__ __forceinline__ static void st(__half* p, float v, float inv_s, float off) {
     *p = __float2half_rn((v - off) * inv_s);
+  }
+  // Stochastic rounding: 13 random bits added below the last FP16 mantissa
+  // bit of the FP32 value's magnitude, then truncation toward zero (exact in
+  // the FP16 normal range; FP16 subnormals, below 6.1e-5 of the scale, keep
+  // a bias toward zero of at most one subnormal step).
+  __device__ __forceinline__ static void st_sr(__half* p, float v, float inv_s, float off, unsigned r) {
+    const unsigned b = __float_as_uint((v - off) * inv_s) + (r >> 19);
+    *p = __float2half_rz(__uint_as_float(b));
   }
 };
 template <> struct Codec<__nv_bfloat16> {
@@ -263,6 +296,12 @@ template <> struct Codec<__nv_bfloat16> {
   __device__ __forceinline__ static __nv_bfloat16 from_bits(unsigned short b) { return __ushort_as_bfloat16(b); }
   __device__ __forceinline__ static void st(__nv_bfloat16* p, float v, float inv_s, float off) {
     *p = __float2bfloat16_rn((v - off) * inv_s);
+  }
+  // Stochastic rounding: 16 random bits added to the FP32 value's magnitude,
+  // then its upper half kept (BF16 shares the FP32 exponent range).
+  __device__ __forceinline__ static void st_sr(__nv_bfloat16* p, float v, float inv_s, float off, unsigned r) {
+    const unsigned b = __float_as_uint((v - off) * inv_s) + (r >> 16);
+    *p = __ushort_as_bfloat16((unsigned short)(b >> 16));
   }
 };
 
@@ -320,6 +359,16 @@ template <typename T, typename L>
 __device__ __forceinline__ void pop_store(T* p, int q, float v, float c) {
   Codec<T>::st(p, v, 1.0f / pow2_scale<L>(q), wprime<L>(q) * c);
 }
+// The per-step store: stochastically rounded in 16-bit storage (the dither
+// stream rng advances once per store), exact in FP32.
+template <typename T, typename L>
+__device__ __forceinline__ void pop_store_sr(T* p, int q, float v, float c, unsigned& rng) {
+  if constexpr (std::is_same<T, float>::value) {
+    *p = v;
+  } else {
+    Codec<T>::st_sr(p, v, 1.0f / pow2_scale<L>(q), wprime<L>(q) * c, dither_next(rng));
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Block-level reduction of the observables into one ring slot.
@@ -329,7 +378,7 @@ struct ObsPartial {
   float vs, ke, cx, cy, cz;
   unsigned int count;
   float mx, mn;
-  unsigned int bad;
+  unsigned int bad;  // status bits: 1 unstable, 2 a bounded wait ran out
 };
 
 __device__ __forceinline__ void obs_init(ObsPartial& o) {
@@ -380,7 +429,8 @@ __device__ inline void obs_block_commit(const ObsPartial& o, DevObs* slot, doubl
   for (int k = 0; k < 6; ++k) v[k] = warp_sum(v[k]);
   unsigned int cnt = warp_usum(o.count);
   float mx = warp_max(o.mx), mn = warp_min(o.mn);
-  unsigned int bad = __any_sync(0xffffffffu, o.bad != 0u) ? 1u : 0u;
+  // status bits: 1 unstable state, 2 a bounded wait ran out
+  unsigned int bad = __reduce_or_sync(0xffffffffu, o.bad);
   if (lane == 0) {
     double* s = scratch + warp * 10;
 #pragma unroll
@@ -393,14 +443,15 @@ __device__ inline void obs_block_commit(const ObsPartial& o, DevObs* slot, doubl
   __syncthreads();
   if (tid == 0) {
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    double c = 0.0, smx = -3.0e38, smn = 3.0e38, sbad = 0.0;
+    double c = 0.0, smx = -3.0e38, smn = 3.0e38;
+    unsigned int sbad = 0u;
     for (int w = 0; w < nwarps; ++w) {
       const double* s = scratch + w * 10;
       for (int k = 0; k < 6; ++k) acc[k] += s[k];
       c += s[6];
       smx = fmax(smx, s[7]);
       smn = fmin(smn, s[8]);
-      sbad += s[9];
+      sbad |= (unsigned int)s[9];
     }
     atomicAdd(&slot->sum_phi, acc[0]);
     atomicAdd(&slot->vol_smooth, acc[1]);
@@ -411,7 +462,7 @@ __device__ inline void obs_block_commit(const ObsPartial& o, DevObs* slot, doubl
     atomicAdd(&slot->vol_count, (unsigned long long)c);
     atomicMax(&slot->phi_max_key, float_key((float)smx));
     atomicMin(&slot->phi_min_key, float_key((float)smn));
-    if (sbad > 0.0) atomicOr(&slot->status, 1u);
+    if (sbad) atomicOr(&slot->status, sbad);
   }
 }
 

@@ -26,6 +26,8 @@ struct pflb_handle {
   int initialized = 0;         // set by pflb_init
   int status = PFLB_OK;
   char err[512] = {0};
+  pflb::TmaMaps* tma[2] = {nullptr, nullptr};  // tensor maps per g source buffer (TMA staging), or null
+  int staging = 1;              // 1: TMA staging where the geometry allows it; 0: cp.async staging
 };
 
 namespace pflb {
@@ -40,6 +42,10 @@ StepArgs handle_step_args(const pflb_handle* h);
 int handle_canon(pflb_handle* h, float* state_dev, int to_canon);
 // Host form of a device observables record.
 void obs_to_host(const DevObs& d, long long step, pflb_obs* o);
+// TMA staging: whether the handle's geometry and family allow it, and the
+// tensor maps of its arrays (returns 1 when built; 0 leaves the cp.async path).
+bool handle_tma_eligible(const pflb_handle* h);
+int handle_build_tma(pflb_handle* h);
 // Records a message and a sticky status on h; returns code.
 int handle_fail(pflb_handle* h, int code, const char* fmt, ...);
 

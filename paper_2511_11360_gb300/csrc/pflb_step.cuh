@@ -20,6 +20,7 @@
 #include "pflb_args.h"
 #include "pflb_mrt.cuh"
 #include "pflb_symsum.cuh"
+#include "pflb_tma.cuh"
 
 namespace pflb {
 
@@ -385,6 +386,23 @@ struct Cell {
   }
 };
 
+// Number of velocities of a lattice with e_x != 0 (their odd-step f reads
+// cross the tile's x edge).
+template <typename L>
+__host__ __device__ constexpr int nsx() {
+  int n = 0;
+  for (int q = 0; q < L::Q; ++q) n += L::ex(q) != 0 ? 1 : 0;
+  return n;
+}
+
+// Rank of velocity q among those with e_x != 0.
+template <typename L>
+__host__ __device__ constexpr int side_rank(int q) {
+  int n = 0;
+  for (int a = 0; a < q; ++a) n += L::ex(a) != 0 ? 1 : 0;
+  return n;
+}
+
 // Number of 16-byte f chunks a block stages per plane (cooperative staging):
 // per velocity and tile row TA / CE chunks, one more on odd steps where e_x != 0.
 template <typename LF, int PAR, int TB, int NCH0>
@@ -397,7 +415,7 @@ __host__ __device__ constexpr int coop_items() {
 // ---------------------------------------------------------------------------
 // Shared-memory footprint of one tile march.
 // ---------------------------------------------------------------------------
-template <int FAM, int DIM, typename T, int TA, int TB, bool COOP = false, int LAT = 0>
+template <int FAM, int DIM, typename T, int TA, int TB, bool COOP = false, int LAT = 0, bool TMA = false, int PAR = 0>
 struct TileSmem {
   static constexpr bool CH = (FAM == FAM_LIANG);
   static constexpr int H = CH ? 2 : 1;
@@ -426,7 +444,12 @@ struct TileSmem {
   // KB, 16 warps, 24.96 -> 25.27 GLUPS at 512^3; D3Q27: three of 67 KB);
   // Cahn-Hilliard tiles have no room for a fourth stage.
   static constexpr int NST = (COOP && !CH && sizeof(T) < 4) ? 4 : 3;
-  static constexpr int STAGE = STAGED ? NST * (FST + GST) : 0;
+  // TMA staging (3D, rows aligned to the population blocks, Allen-Cahn
+  // halo): NST stages in the box layout of TmaStage, 128-byte aligned (plus
+  // 128 bytes of slack to align the dynamic base), then NST mbarriers.
+  using TS = TmaStage<TB, (DIM == 3 && !CH) ? Lattices<DIM, LAT>::G::Q - 1 : Lattices<DIM, LAT>::G::Q,
+                      Lattices<DIM, LAT>::F::Q, nsx<typename Lattices<DIM, LAT>::F>(), (int)sizeof(T), PAR>;
+  static constexpr int STAGE = TMA ? (NST * TS::BYTES + 128 + 8 * NST) / 4 : (STAGED ? NST * (FST + GST) : 0);
   static_assert(!COOP || (FST % 4 == 0 && GST % 4 == 0), "16-byte aligned stages");
   static constexpr size_t BYTES = (size_t)(STAGE + PHI + MU) * sizeof(float);
 };
@@ -437,10 +460,11 @@ struct TileSmem {
 // kernel (one tile per block) and by the persistent batch kernel (tiles of
 // many domains claimed in turn). Accumulates the observables into obs.
 // ---------------------------------------------------------------------------
-template <int FAM, int DIM, typename T, int TA, int TB, int PAR = -1, int ROW = -1, int LAT = 0>
+template <int FAM, int DIM, typename T, int TA, int TB, int PAR = -1, int ROW = -1, int LAT = 0, bool TMA = false>
 __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, int c0, int chunk,
                                           float* __restrict__ s_phi, float* __restrict__ s_mu,
-                                          float* __restrict__ s_stage, ObsPartial& obs) {
+                                          float* __restrict__ s_stage, ObsPartial& obs,
+                                          const TmaMaps* tm = nullptr) {
   using LG = typename Lattices<DIM, LAT>::G;
   using LF = typename Lattices<DIM, LAT>::F;
   using LS = typename Lattices<DIM, LAT>::S;
@@ -461,7 +485,11 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
   // COOP: the block stages f together in 16-byte chunks (3D, rows aligned to
   // the population blocks, AA parity known at compile time).
   constexpr bool COOP = (DIM == 3) && (ROW == 1) && (PAR >= 0);
-  using SMEM = TileSmem<FAM, DIM, T, TA, TB, COOP, LAT>;
+  // TMA: the block-staged geometry with its copies made by the tensor
+  // memory accelerator (the host guarantees ny % TB == 0 for it).
+  constexpr bool TMAS = TMA && COOP && !CH && TA == 32;
+  static_assert(!TMA || TMAS, "TMA staging needs the row-aligned 3D Allen-Cahn tile");
+  using SMEM = TileSmem<FAM, DIM, T, TA, TB, COOP, LAT, TMAS, (PAR == 1 ? 1 : 0)>;
   constexpr bool STAGED = SMEM::STAGED;
   constexpr int FST = SMEM::FST, GST = SMEM::GST;
   constexpr int NST = SMEM::NST;
@@ -699,10 +727,10 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
   // offsets (plane term excluded, z neighbour included) and stage offsets.
   constexpr int NCH0 = TA / CE;
   constexpr int NFI = coop_items<LF, PAR, TB, NCH0>();
-  constexpr int KF = COOP ? (NFI + NT - 1) / NT : 1;
-  unsigned fsrc[KF], fdst[KF];
+  constexpr int KF = (COOP && !TMAS) ? (NFI + NT - 1) / NT : 1;
+  unsigned fsrc[KF] = {}, fdst[KF] = {};
   unsigned fmz = 0u, fpz = 0u;   // items reading plane c - 1 / c + 1
-  if constexpr (COOP) {
+  if constexpr (COOP && !TMAS) {
 #pragma unroll
     for (int k = 0; k < KF; ++k) {
       fsrc[k] = 0u;
@@ -821,6 +849,149 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
     }
   };
 
+  // ------------------------------------------------------------------ TMA
+  // Stage s holds plane c's g (the tile's rows and both halo rows; the x
+  // halo in two side boxes) and its f, in the box layout of TmaStage; the
+  // copies of stage s complete on barrier s. Warp 0 issues them, one box per
+  // lane: item 0 the g main box, 1 and 2 the g side boxes, then the f boxes
+  // (even steps: one box of every slot; odd steps: one box per velocity,
+  // slot opp(q) of the rows shifted by -e_q, then one 16-byte side box per
+  // velocity with e_x != 0). A box whose rows cross the domain's y edge is
+  // zero-filled there by the TMA unit; the threads that need such a wrapped
+  // row (a halo row of g, one row of f for e_y != 0) read it from global
+  // memory instead.
+  using TS = typename SMEM::TS;
+  static_assert(!TMAS || TS::ALIGNED, "TMA boxes must land 128-byte aligned");
+  constexpr int QGS = SKIP0 ? QG - 1 : QG;   // staged g slots (Q0 .. QG - 1)
+  constexpr int Q0 = SKIP0 ? 1 : 0;
+  constexpr int SL = TS::SL;
+  constexpr int ES = (int)sizeof(T);
+  constexpr int NITEMS = 3 + (PAR == 1 ? QF + nsx<LF>() : 1);
+  constexpr int KI = TMAS ? (NITEMS + 31) / 32 : 1;
+  unsigned tstage = 0u, tbar = 0u;   // shared addresses of stage 0 and barrier 0
+  const char* tgen = nullptr;        // generic address of stage 0
+  unsigned tphase = 0u;              // parity of each stage's next completion (bit s)
+  bool tmo = false;                  // a bounded wait ran out
+  int cstop = c1;
+  int it_map[KI], it_c0[KI], it_c1[KI], it_dxb[KI], it_dy[KI], it_dz[KI], it_dst[KI];
+  bool it_g[KI];
+  int hoff[KH], hqs[KH];             // halo cell: byte offset of its first staged g slot, slot stride
+  bool hglob[KH];                    // halo cell in a row beyond the y edge: read from global memory
+  int own_goff = 0;
+  const int NXB = NA / 32, xb0 = a0 / 32;
+  if constexpr (TMAS) {
+    tstage = (smem_u32(s_stage) + 127u) & ~127u;
+    tbar = tstage + (unsigned)(NST * TS::BYTES);
+    tgen = reinterpret_cast<const char*>(s_stage) + (tstage - smem_u32(s_stage));
+    own_goff = TS::G_MAIN + ((ty + 1) * QGS * 32 + tx) * ES;
+#pragma unroll
+    for (int k = 0; k < KH; ++k) {
+      hoff[k] = 0;
+      hqs[k] = 0;
+      hglob[k] = false;
+      if (halo_pos[k] >= 0) {
+        const int rb = halo_pos[k] / RA, ra = halo_pos[k] % RA;
+        hglob[k] = (rb == 0 && b0 == 0) || (rb == TB + 1 && b0 + TB >= NB);
+        if (ra == 0) { hoff[k] = TS::G_LEFT + (rb * QGS * SL + SL - 1) * ES; hqs[k] = SL * ES; }
+        else if (ra == TA + 1) { hoff[k] = TS::G_RIGHT + (rb * QGS * SL) * ES; hqs[k] = SL * ES; }
+        else { hoff[k] = TS::G_MAIN + (rb * QGS * 32 + ra - 1) * ES; hqs[k] = 32 * ES; }
+      }
+    }
+    const int lane = tid & 31;
+#pragma unroll
+    for (int ki = 0; ki < KI; ++ki) {
+      const int i = lane + 32 * ki;
+      it_map[ki] = -1;
+      it_c0[ki] = it_c1[ki] = it_dxb[ki] = it_dy[ki] = it_dz[ki] = it_dst[ki] = 0;
+      it_g[ki] = false;
+      if (i < 3) {
+        it_g[ki] = true;
+        it_map[ki] = i == 0 ? TM_G_MAIN : TM_G_SIDE;
+        it_c0[ki] = i == 1 ? 32 - SL : 0;
+        it_c1[ki] = Q0;
+        it_dxb[ki] = i == 0 ? 0 : (i == 1 ? -1 : 1);
+        it_dy[ki] = -1;
+        it_dst[ki] = i == 0 ? TS::G_MAIN : (i == 1 ? TS::G_LEFT : TS::G_RIGHT);
+      } else if (PAR == 0 && i == 3) {
+        it_map[ki] = TM_F_ALL;
+        it_dst[ki] = TS::F;
+      } else if (PAR == 1 && i < NITEMS) {
+        const bool side = i >= 3 + QF;
+        // velocity q of the item: i - 3, or for a side item the
+        // (i - 3 - QF)-th velocity with e_x != 0 (selected at compile time)
+        int q = 0, ex = 0, ey = 0, ez = 0, oq = 0;
+        static_for<0, QF>([&](auto qc) {
+          constexpr int qq = decltype(qc)::value;
+          const bool hit = side ? (LF::ex(qq) != 0 && side_rank<LF>(qq) == i - 3 - QF) : (qq == i - 3);
+          if (hit) {
+            q = qq;
+            ex = LF::ex(qq);
+            ey = LF::ey(qq);
+            ez = LF::ez(qq);
+            oq = LF::opp(qq);
+          }
+        });
+        it_map[ki] = side ? TM_F_SIDE : TM_F_MAIN;
+        it_c0[ki] = side && ex > 0 ? 32 - SL : 0;
+        it_c1[ki] = oq;
+        it_dxb[ki] = side ? (ex > 0 ? -1 : 1) : 0;
+        it_dy[ki] = -ey;
+        it_dz[ki] = -ez;
+        it_dst[ki] = side ? TS::F_SIDE + (i - 3 - QF) * TS::F_SIDE_STRIDE : TS::F + q * TB * 32 * ES;
+        (void)ex;
+      }
+    }
+    if (tid == 0) {
+      for (int k = 0; k < NST; ++k) mbar_init(tbar + 8u * k, 1u);
+      mbar_init_fence();
+    }
+    __syncthreads();
+  }
+  // Warp 0: the copies of g of plane cg and f of plane cf into stage s.
+  auto tma_issue = [&](int cg, int cf, int s) {
+    const unsigned bar = tbar + 8u * (unsigned)s, base = tstage + (unsigned)(s * TS::BYTES);
+    if ((tid & 31) == 0) mbar_arrive_expect_tx(bar, TS::TX);
+    __syncwarp();
+    const int pg = wrap_mod(cg, NC);
+#pragma unroll
+    for (int ki = 0; ki < KI; ++ki) {
+      if (it_map[ki] < 0) continue;
+      const int z = wrap_mod((it_g[ki] ? pg : cf) + it_dz[ki], NC);
+      const int xb = wrap_mod(xb0 + it_dxb[ki], NXB);
+      // y may be -1 or run past ny - 1: those rows are zero-filled
+      tma_load5(base + (unsigned)it_dst[ki], &tm->m[it_map[ki]], it_c0[ki], it_c1[ki], xb, b0 + it_dy[ki], z, bar);
+    }
+  };
+  // phi of logical plane c from TMA stage s into the ring; keeps the own cell's g.
+  auto produce_tma = [&](int c, int s, float (&gown)[QG]) {
+    const char* base = tgen + s * TS::BYTES;
+    float* slot = ring(c);
+#pragma unroll
+    for (int q = 0; q < QG; ++q)
+      gown[q] = (q < Q0) ? 0.0f
+                         : Codec<T>::dec(*reinterpret_cast<const T*>(base + own_goff + (q - Q0) * 32 * ES),
+                                         pow2_scale<LG>(q), wprime<LG>(q) * P.gref);
+    slot[own_slot] = finish_phi<FAM>(P, phi_star<LG, SKIP0>(gown), gamma);
+#pragma unroll
+    for (int k = 0; k < KH; ++k) {
+      if (halo_pos[k] >= 0) {
+        float tmp[QG];
+        float hs;
+        if (hglob[k]) {   // a wrapped halo row: from global memory
+          hs = load_g(halo_ab[k] + (unsigned)(NAB * map_c(c)), tmp);
+        } else {
+#pragma unroll
+          for (int q = 0; q < QG; ++q)
+            tmp[q] = (q < Q0) ? 0.0f
+                              : Codec<T>::dec(*reinterpret_cast<const T*>(base + hoff[k] + (q - Q0) * hqs[k]),
+                                              pow2_scale<LG>(q), wprime<LG>(q) * P.gref);
+          hs = phi_star<LG, SKIP0>(tmp);
+        }
+        slot[halo_pos[k]] = finish_phi<FAM>(P, hs, gamma);
+      }
+    }
+  };
+
   float g0[QG], g1[QG], g2[QG];
   // Prologue: planes c0-H .. c0+H-1.
   {
@@ -839,7 +1010,14 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
   // after the next plane's first barrier, so one of the NST is always being
   // drained.
   constexpr int AHEAD = COOP ? NST - 1 : NST;
-  if constexpr (STAGED) {
+  if constexpr (TMAS) {
+#pragma unroll
+    for (int k = 0; k < NST; ++k) gmq[k] = fmq[k] = 0u;
+    if (tid < 32) {
+      for (int k = 0; k < AHEAD; ++k)
+        if (c0 + k < c1) tma_issue(c0 + k + H, c0 + k, k);
+    }
+  } else if constexpr (STAGED) {
 #pragma unroll
     for (int k = 0; k < NST; ++k) {
       gmq[k] = fmq[k] = 0u;
@@ -855,7 +1033,13 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
 
   for (int c = c0; c < c1; ++c) {
     const unsigned gms = gmq[0], fms = fmq[0];
-    if constexpr (STAGED) cp_async_wait<AHEAD - 1>();   // plane c has landed; the later ones may be in flight
+    bool landed = true;
+    if constexpr (TMAS) {
+      landed = mbar_wait_bounded(tbar + 8u * (unsigned)st, (tphase >> st) & 1u);   // plane c's copies
+      tphase ^= 1u << st;
+    } else if constexpr (STAGED) {
+      cp_async_wait<AHEAD - 1>();   // plane c has landed; the later ones may be in flight
+    }
     if constexpr (CH) {
       if constexpr (STAGED) produce_staged(c + 2, st, gms, g2);
       else produce(c + 2, g2);
@@ -863,18 +1047,34 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
       make_mu(c + 1);
       __syncthreads();
     } else {
-      if constexpr (STAGED) produce_staged(c + 1, st, gms, g1);
-      else produce(c + 1, g1);
-      __syncthreads();
+      if constexpr (TMAS) {
+        produce_tma(c + 1, st, g1);
+        // this thread's reads of the stage of plane c - 1 come before the
+        // copies that refill it (generic -> async proxy)
+        fence_proxy_async();
+        if (__syncthreads_or(landed ? 0 : 1)) {
+          tmo = true;
+          cstop = c;
+          break;
+        }
+      } else {
+        if constexpr (STAGED) produce_staged(c + 1, st, gms, g1);
+        else produce(c + 1, g1);
+        __syncthreads();
+      }
     }
     if constexpr (COOP) {
       // Every thread is past plane c - 1: refill its stage with plane c + NST - 1.
       const int sn = (st == 0) ? NST - 1 : st - 1;
-      unsigned gnext = 0u, fnext = 0u;
-      if (c + NST - 1 < c1) issue(c + NST - 1 + H, c + NST - 1, sn, gnext, fnext);
-      cp_async_commit();
-      gmq[NST - 1] = gnext;
-      fmq[NST - 1] = fnext;
+      if constexpr (TMAS) {
+        if (tid < 32 && c + NST - 1 < c1) tma_issue(c + NST - 1 + H, c + NST - 1, sn);
+      } else {
+        unsigned gnext = 0u, fnext = 0u;
+        if (c + NST - 1 < c1) issue(c + NST - 1 + H, c + NST - 1, sn, gnext, fnext);
+        cp_async_commit();
+        gmq[NST - 1] = gnext;
+        fmq[NST - 1] = fnext;
+      }
     }
 
     if (active) {
@@ -918,7 +1118,40 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
 
       // Pre-collision f (AA pattern).
       float f[QF];
-      if constexpr (COOP) {
+      if constexpr (TMAS) {
+        // Even steps: row ty of the all-slot box. Odd steps: row ty of
+        // velocity q's box holds the cells x0 - e_x .. x0 + 31 - e_x shifted
+        // into lanes; the one lane whose source lies beyond the tile's x edge
+        // reads the side box (lane SL - 1 of the left block for e_x = +1,
+        // lane 0 of the right block for e_x = -1).
+        const char* fst = tgen + st * TS::BYTES;
+        static_for<0, QF>([&](auto qc) {
+          constexpr int q = decltype(qc)::value;
+          T v;
+          if constexpr (PAR == 0) {
+            v = *reinterpret_cast<const T*>(fst + TS::F + ((ty * QF + q) * 32 + tx) * ES);
+          } else {
+            constexpr int ex = LF::ex(q), ey = LF::ey(q);
+            // the box's row ty lies beyond the y edge (wrapped): global memory
+            const bool wrapped = (ey > 0 && ty == 0 && b0 == 0) || (ey < 0 && ty == TB - 1 && b0 + TB >= NB);
+            if (wrapped) {
+              constexpr int dc = dc_of<DIM, LF>(q);
+              v = Codec<T>::ldc(fb + f_cell(-ex, -ey, plane_of(c, -dc)) + LF::opp(q) * kPopBlock);
+            } else {
+              const char* mainp = fst + TS::F + ((q * TB + ty) * 32 + tx - ex) * ES;
+              if constexpr (ex == 0) {
+                v = *reinterpret_cast<const T*>(mainp);
+              } else {
+                constexpr int sidx = side_rank<LF>(q);
+                const char* sidep = fst + TS::F_SIDE + sidx * TS::F_SIDE_STRIDE + (ty * SL + (ex > 0 ? SL - 1 : 0)) * ES;
+                const bool out = ex > 0 ? (tx == 0) : (tx == TA - 1);
+                v = *reinterpret_cast<const T*>(out ? sidep : mainp);
+              }
+            }
+          }
+          f[q] = Codec<T>::dec(v, pow2_scale<LF>(q), 0.0f);
+        });
+      } else if constexpr (COOP) {
         // Row (q, ty) of the stage; an odd step's x - e_q sits at tx - e_x
         // from the row's x0 (+ CE where the row starts at x0 - CE).
         const T* fs = reinterpret_cast<const T*>(stage_f(st)) + ty * FROW + tx;
@@ -987,18 +1220,19 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
         }
         // g: two-array push, bounce-back into the own cell at walls.
         const float uw_lo = P.moving ? P.wall_u[0] : 0.0f, uw_hi = P.moving ? P.wall_u[1] : 0.0f;
+        unsigned rng = WIDE ? 0u : dither_seed(idx, args.seed);   // 16-bit storage: stochastic rounding
 #pragma unroll
         for (int q = 0; q < QG; ++q) {
           if (DIM == 3 && !CH && q == 0) continue;
           const int da = da_of<DIM, LG>(q), db = db_of<DIM, LG>(q), dc = dc_of<DIM, LG>(q);
           if (P.freeze) {
-            pop_store<T, LG>(gdst + g_cell(0, 0, c) + q * kPopBlock, q, g0[q], P.gref);
+            pop_store_sr<T, LG>(gdst + g_cell(0, 0, c) + q * kPopBlock, q, g0[q], P.gref, rng);
           } else if (crosses(dc)) {
             const float uw = dc < 0 ? uw_lo : uw_hi;
             const float v = gnew[q] - 6.0f * LG::w(q) * pc * (float)LG::ex(q) * uw;
-            pop_store<T, LG>(gdst + g_cell(0, 0, c) + LG::opp(q) * kPopBlock, q, v, P.gref);
+            pop_store_sr<T, LG>(gdst + g_cell(0, 0, c) + LG::opp(q) * kPopBlock, q, v, P.gref, rng);
           } else {
-            pop_store<T, LG>(gdst + g_cell(da, db, plane_of(c, dc)) + q * kPopBlock, q, gnew[q], P.gref);
+            pop_store_sr<T, LG>(gdst + g_cell(da, db, plane_of(c, dc)) + q * kPopBlock, q, gnew[q], P.gref, rng);
           }
         }
         // f: AA pattern.
@@ -1013,9 +1247,9 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
             v -= 6.0f * LF::w(q) * sc * (float)LF::ex(q) * uw;
           }
           if (parity == 0 || cr) {
-            pop_store<T, LF>(fb + f_cell(0, 0, c) + LF::opp(q) * kPopBlock, q, v, 0.0f);
+            pop_store_sr<T, LF>(fb + f_cell(0, 0, c) + LF::opp(q) * kPopBlock, q, v, 0.0f, rng);
           } else {
-            pop_store<T, LF>(fb + f_cell(da, db, plane_of(c, dc)) + q * kPopBlock, q, v, 0.0f);
+            pop_store_sr<T, LF>(fb + f_cell(da, db, plane_of(c, dc)) + q * kPopBlock, q, v, 0.0f, rng);
           }
         }
       }
@@ -1050,6 +1284,22 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
     }
   }
 
+  if constexpr (TMAS) {
+    if (tmo) {
+      // A stage's copies did not land within the poll limit: report it and
+      // wait (bounded again) for the copies still in flight -- those of the
+      // planes cstop .. cstop + NST - 2 -- before the block exits.
+      obs.bad |= kStatusTimeout;
+      for (int j = 0; j + 1 < NST; ++j) {
+        if (cstop + j >= c1) break;
+        const int s = (st + j) % NST;
+        const unsigned par = ((tphase >> s) & 1u) ^ (j == 0 ? 1u : 0u);
+        (void)mbar_wait_bounded(tbar + 8u * (unsigned)s, par);
+      }
+    }
+  }
+  (void)cstop;
+  (void)tmo;
   // Centroid moments along the fast axes, whose coordinates are fixed per
   // thread (inactive threads added nothing to vs).
   obs.cx += (float)aw * obs.vs;
@@ -1059,7 +1309,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
   // attained at phi_min or phi_max (mn <= mx once a cell was visited).
   if (obs.mn <= obs.mx) {
     const float r1 = P.rhoL + P.drho_dphi * (obs.mn - P.phiL), r2 = P.rhoL + P.drho_dphi * (obs.mx - P.phiL);
-    if (!(isfinite(obs.s_hi) && isfinite(obs.ke) && r1 > 0.0f && r2 > 0.0f)) obs.bad = 1u;
+    if (!(isfinite(obs.s_hi) && isfinite(obs.ke) && r1 > 0.0f && r2 > 0.0f)) obs.bad |= 1u;
   }
 }
 
@@ -1092,9 +1342,51 @@ step_kernel(const StepArgs args) {
   obs_block_commit(obs, args.obs_slot, s_red);
 }
 
+// The single-domain kernel with TMA staging (3D, nx a multiple of 32, ny a
+// multiple of TB, Allen-Cahn halo): the tensor maps of this step's arrays
+// come by value in parameter space.
+template <int FAM, int DIM, typename T, int PAR, int LAT>
+__global__ void __launch_bounds__(Geom<FAM, DIM, T, LAT>::TA * Geom<FAM, DIM, T, LAT>::TB, Geom<FAM, DIM, T, LAT>::MINB)
+step_kernel_tma(const StepArgs args, const __grid_constant__ TmaMaps tm) {
+  constexpr int TA = Geom<FAM, DIM, T, LAT>::TA, TB = Geom<FAM, DIM, T, LAT>::TB;
+  using SM = TileSmem<FAM, DIM, T, TA, TB, true, LAT, true, PAR>;
+  extern __shared__ __align__(128) float dyn_smem_tma[];
+  float* s_stage = dyn_smem_tma;
+  float* s_phi = dyn_smem_tma + SM::STAGE;
+  float* s_mu = s_phi + SM::PHI;
+  __shared__ double s_red[(TA * TB / 32) * 10];
+  const int NA = args.p.nx, NB = args.p.ny;
+  const int tiles_a = (NA + TA - 1) / TA, tiles_b = (NB + TB - 1) / TB;
+  int bid = blockIdx.x;
+  const int ti = bid % tiles_a;
+  bid /= tiles_a;
+  const int tj = bid % tiles_b;
+  bid /= tiles_b;
+  if (args.obs_zero != nullptr && blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+    obs_zero_slot(args.obs_zero);
+  ObsPartial obs;
+  obs_init(obs);
+  step_tile<FAM, DIM, T, TA, TB, PAR, 1, LAT, true>(args, ti * TA, tj * TB, bid * args.chunk, args.chunk, s_phi, s_mu,
+                                                    s_stage, obs, &tm);
+  obs_block_commit(obs, args.obs_slot, s_red);
+}
+
 template <int FAM, int DIM, typename T, int PAR, int ROW, int LAT>
 void launch_step_par(const StepArgs& args, cudaStream_t stream) {
   constexpr int TA = Geom<FAM, DIM, T, LAT>::TA, TB = Geom<FAM, DIM, T, LAT>::TB;
+  if constexpr (DIM == 3 && ROW == 1 && FAM != FAM_LIANG && TA == 32) {
+    if (args.tma != nullptr && args.p.ny % TB == 0) {
+      constexpr size_t smem = TileSmem<FAM, DIM, T, TA, TB, true, LAT, true, PAR>::BYTES;
+      static const cudaError_t attr = cudaFuncSetAttribute(
+          step_kernel_tma<FAM, DIM, T, PAR, LAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      (void)attr;
+      const long long tiles = (long long)(args.p.nx / TA) * (args.p.ny / TB);
+      const long long chunks = (args.p.nz + args.chunk - 1) / args.chunk;
+      step_kernel_tma<FAM, DIM, T, PAR, LAT><<<(unsigned)(tiles * chunks), dim3(TA, TB, 1), smem, stream>>>(
+          args, *args.tma);
+      return;
+    }
+  }
   constexpr size_t smem = TileSmem<FAM, DIM, T, TA, TB, (DIM == 3) && (ROW == 1) && (PAR >= 0), LAT>::BYTES;
   static const cudaError_t attr = cudaFuncSetAttribute(
       step_kernel<FAM, DIM, T, PAR, ROW, LAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -101,6 +101,8 @@ SIGNATURES = {
     "pflb_step_count": (ctypes.c_int64, [ctypes.c_void_p]),
     "pflb_bytes_per_update": (ctypes.c_double, [ctypes.c_void_p]),
     "pflb_set_chunk": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "pflb_set_staging": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "pflb_get_staging": (ctypes.c_int, [ctypes.c_void_p]),
     "pflb_lattice": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                     ctypes.c_void_p, ctypes.c_void_p]),
     "pflb_destroy": (ctypes.c_int, [ctypes.c_void_p]),
@@ -267,6 +269,15 @@ class Sim:
 
     def set_chunk(self, c):
         return self._check(self.lib.pflb_set_chunk(self.h, int(c)))
+
+    def set_staging(self, mode):
+        """1: TMA staging where the geometry allows it (default); 0: cp.async."""
+        return self._check(self.lib.pflb_set_staging(self.h, int(mode)))
+
+    @property
+    def staging(self):
+        """1 if the next step uses TMA staging, else 0."""
+        return int(self.lib.pflb_get_staging(self.h))
 
     def bytes_per_update(self):
         return float(self.lib.pflb_bytes_per_update(self.h))

@@ -32,3 +32,32 @@ def pytest_terminal_summary(terminalreporter, exitstatus, config):
         import json
         with open(path, "w") as fh:
             json.dump(rec, fh, indent=1)
+
+
+def _gpu_session(session):
+    if not any(item.get_closest_marker("gpu") for item in session.items):
+        return False
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def pytest_collection_finish(session):
+    """A session that runs the long-trajectory GPU tests starts their FP64
+    oracle runs (tests/long_jobs.py, spawned processes) right after
+    collection, so they overlap with the GPU test modules that run first."""
+    names = {item.module.__name__ for item in session.items if hasattr(item, "module")}
+    if not ({"test_gpu_rt", "test_gpu_turbulence"} & names):
+        return
+    if not _gpu_session(session):
+        return
+    import long_jobs
+    long_jobs.start()
+
+
+def pytest_sessionfinish(session, exitstatus):
+    mod = sys.modules.get("long_jobs")
+    if mod is not None:
+        mod.shutdown()

@@ -1,9 +1,8 @@
 """Parity at the full sizes of the benchmark workloads, in the launch
 configuration the benchmark uses (default block chunking).
 
-  * 2D Rayleigh-Taylor, 256 x 1024, walls, Atwood 0.5, all five families:
-    whole-field comparison with the FP64 oracle after 50 steps (an unstable
-    flow: the bound widens to 3x the oracle's own sensitivity if needed).
+  (2D Rayleigh-Taylor at 256 x 1024 is compared over 1000 steps in
+  test_gpu_rt.py.)
   * 3D droplet-laden turbulence, 512^3, 200 droplets, Fakhari2017, FP32 and
     FP16 storage: one step checked at sampled cells (each recomputed by the
     oracle on a periodic patch of radius 2 around the cell from the GPU's
@@ -17,7 +16,7 @@ import oracle as O
 from paper_2511_11360_gb300 import cases as C
 from paper_2511_11360_gb300 import pflb
 
-from gpu_common import check_parity, make_sim, oracle_start, require_gpu, torch
+from gpu_common import require_gpu, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -28,16 +27,6 @@ FID = [C.FAMILY_NAMES[f] for f in FAMS]
 @pytest.fixture(scope="module", autouse=True)
 def _gpu():
     require_gpu()
-
-
-@pytest.mark.parametrize("fam", FAMS, ids=FID)
-def test_rayleigh_taylor_256x1024(fam):
-    P, phi, u = C.rayleigh_taylor_2d(nx=256, ny=1024, family=fam)
-    sim = make_sim(P, phi, u)
-    sim.step(50)
-    sim.sync()
-    e = check_parity(sim, P, phi, u, 50)
-    print("RT %s: phi %.2e u %.2e (bounds %.1e %.1e)" % (C.FAMILY_NAMES[fam], *e))
 
 
 @pytest.fixture(scope="module")

@@ -59,6 +59,13 @@ def small_case(kind, fam):
                                         centre=(0.3, 0.5, 0.5))
         P.update(rho_H=2.0, rho_L=1.0, nu_L=0.05)
         return P, phi, u, 3
+    if kind == "3d_tma":
+        # nx a multiple of 32 and ny a multiple of the 4-row tile: TMA
+        # staging (edge tiles in y at both ends, one interior tile)
+        P, phi, u = C.droplet_in_tgv_3d(nx=64, ny=12, nz=9, R=4.0, W=3.0, family=fam,
+                                        centre=(0.3, 0.45, 0.5))
+        P.update(rho_H=2.0, rho_L=1.0, nu_L=0.05)
+        return P, phi, u, 3
     raise ValueError(kind)
 
 
@@ -93,6 +100,12 @@ def laminar_case(kind, fam):
                                         centre=(0.37, 0.58, 0.44), phase=(0.4, 1.1, 0.7))
         P.update(rho_H=2.0, rho_L=1.0, nu_L=0.05)
         return P, phi, u, 4
+    if kind == "3d_tma":
+        # the same flow on 64 x 20 x 18 (TMA staging)
+        P, phi, u = C.droplet_in_tgv_3d(nx=64, ny=20, nz=18, R=6.0, W=3.0, family=fam,
+                                        centre=(0.37, 0.58, 0.44), phase=(0.4, 1.1, 0.7))
+        P.update(rho_H=2.0, rho_L=1.0, nu_L=0.05)
+        return P, phi, u, 4
     raise ValueError(kind)
 
 
@@ -105,7 +118,7 @@ STORAGE_TOL = {0: 2e-6, 1: 1.5e-3, 2: 1.2e-2}   # relative to max |population|
 
 
 @pytest.mark.parametrize("storage", [0, 1, 2], ids=["fp32", "fp16", "bf16"])
-@pytest.mark.parametrize("kind", ["2d", "2d_walls", "2d_moving", "3d", "3d_row"])
+@pytest.mark.parametrize("kind", ["2d", "2d_walls", "2d_moving", "3d", "3d_row", "3d_tma"])
 @pytest.mark.parametrize("fam", FAMS, ids=FID)
 def test_one_step_canonical_parity(fam, kind, storage):
     """Init and two steps (an even and an odd AA step): the GPU's canonical
@@ -130,7 +143,7 @@ def test_one_step_canonical_parity(fam, kind, storage):
 
 
 # ------------------------------------------------------- 1000-step parity
-@pytest.mark.parametrize("kind", ["2d", "2d_static", "2d_walls", "2d_moving", "3d", "3d_row"])
+@pytest.mark.parametrize("kind", ["2d", "2d_static", "2d_walls", "2d_moving", "3d", "3d_row", "3d_tma"])
 @pytest.mark.parametrize("fam", FAMS, ids=FID)
 def test_laminar_1000_steps_fp32(fam, kind):
     """phi and u after 1000 steps within 1e-5 (relative L-infinity) of the FP64
@@ -142,6 +155,22 @@ def test_laminar_1000_steps_fp32(fam, kind):
     u_ref = P["sigma"] / (P["rho_H"] * P["nu_H"]) if kind == "2d_static" else None
     e = check_parity(sim, P, phi, u, 1000, u_ref=u_ref)
     print("%s %s: phi %.2e u %.2e (bounds %.1e %.1e)" % (C.FAMILY_NAMES[fam], kind, *e))
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3], ids=["mu_linear", "mu_inverse", "mu_log"])
+@pytest.mark.parametrize("kind", ["2d", "3d_tma"])
+@pytest.mark.parametrize("fam", FAMS, ids=FID)
+def test_viscosity_interpolations_1000_steps(fam, kind, mode):
+    """The dynamic-viscosity interpolations of Eqs. (mu_linear), (mu_inverse)
+    and (mu_log) with a density and viscosity contrast (rho 2 : 1, mu 4 : 1):
+    phi and u after 1000 steps against the oracle (bar as check_parity)."""
+    P, phi, u, chunk = laminar_case(kind, fam)
+    P = dict(P, visc_interp=mode, rho_H=2.0, rho_L=1.0, nu_H=0.1, nu_L=0.05)
+    sim = make_sim(P, phi, u, chunk=chunk)
+    sim.step(1000)
+    sim.sync()
+    e = check_parity(sim, P, phi, u, 1000)
+    print("%s %s visc %d: phi %.2e u %.2e (bounds %.1e %.1e)" % (C.FAMILY_NAMES[fam], kind, mode, *e))
 
 
 # ---------------------------------------------------------------- observables
@@ -317,3 +346,66 @@ def test_step_is_mirror_exact(fam, kind, axis):
     a.step(20)
     b.step(20)
     assert np.array_equal(_mirror_state(P, a.save(), axis), b.save())
+
+
+# ------------------------------------------------------------ TMA staging
+TMA_FAMS = [C.FAKHARI2017, C.CHAI2018, C.HU2019, C.LIANG2018]
+
+
+@pytest.mark.parametrize("lat", [19, 27], ids=["d3q19", "d3q27_mrt"])
+@pytest.mark.parametrize("storage", [0, 1, 2], ids=["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("fam", TMA_FAMS, ids=[C.FAMILY_NAMES[f] for f in TMA_FAMS])
+@pytest.mark.parametrize("shape", [(64, 12, 9), (32, 8, 5), (96, 16, 7)], ids=["64x12x9", "32x8x5", "96x16x7"])
+def test_tma_staging_matches_cp_async_bitwise(shape, fam, storage, lat):
+    """The TMA-staged step (bulk tensor copies of the tile and its halo,
+    completed on shared-memory barriers) reads exactly the populations the
+    cp.async-staged step reads, so every state is bit for bit the same: over
+    even and odd AA steps, edge and interior tiles in y, one x-block (periodic
+    wrap onto itself) and several, ragged chunks in z."""
+    nx, ny, nz = shape
+    P, phi, u = C.droplet_in_tgv_3d(nx=nx, ny=ny, nz=nz, R=3.0, W=2.5, family=fam, centre=(0.3, 0.45, 0.5))
+    P.update(rho_H=2.0, rho_L=1.0, nu_L=0.05)
+    if lat == 27:
+        P.update(lattice_f=27, collision=1, mrt_s_bulk=1.1, mrt_s_ho=1.4)
+    a = make_sim(P, phi, u, storage=storage, chunk=3)
+    b = make_sim(P, phi, u, storage=storage, chunk=3)
+    b.set_staging(0)
+    assert a.staging == 1 and b.staging == 0
+    # Chai2018 / Hu2019 take gamma from FP64 atomic sums, whose order varies
+    # from run to run: their states agree to rounding, the others bit for bit.
+    exact = fam not in (C.CHAI2018, C.HU2019)
+    for n in (1, 1, 5):
+        a.step(n)
+        b.step(n)
+        sa, sb = a.save(), b.save()
+        if exact:
+            assert np.array_equal(sa, sb)
+        else:
+            assert np.max(np.abs(sa - sb)) <= 1e-6 * np.max(np.abs(sb))
+    # the fields are FP32 arithmetic on identical populations; in 16-bit
+    # storage the two kernel instantiations may contract a multiply-add
+    # differently, a last-bit difference the 16-bit populations do not see
+    for x, y in zip(a.fields(), b.fields()):
+        if exact and storage == 0:
+            assert np.array_equal(x, y)
+        else:
+            assert np.max(np.abs(x - y)) <= 1e-6 * max(np.max(np.abs(y)), 1e-30)
+    oa, ob = a.observables(), b.observables()
+    assert oa["vol_count"] == ob["vol_count"] and abs(oa["sum_phi"] / ob["sum_phi"] - 1) < 1e-12
+
+
+@pytest.mark.parametrize("shape,fam,tma", [((64, 11, 9), C.FAKHARI2017, 0), ((35, 12, 9), C.FAKHARI2017, 0),
+                                          ((64, 4, 9), C.FAKHARI2017, 0), ((64, 12, 9), C.LIANG2014, 0),
+                                          ((64, 12, 9), C.FAKHARI2017, 1)])
+def test_tma_staging_where_the_geometry_allows(shape, fam, tma):
+    """TMA staging is used for 3D domains with nx a multiple of 32 and ny a
+    multiple of the tile's 4 rows (at least 8), Allen-Cahn families; elsewhere
+    the step falls back to cp.async staging."""
+    nx, ny, nz = shape
+    P, phi, u = C.droplet_in_tgv_3d(nx=nx, ny=ny, nz=nz, R=3.0, W=2.5, family=fam)
+    s = make_sim(P, phi, u)
+    assert s.staging == tma
+    s.set_staging(0)
+    assert s.staging == 0
+    with pytest.raises(pflb.PflbError):
+        s.set_staging(2)

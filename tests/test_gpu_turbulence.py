@@ -1,0 +1,148 @@
+"""Chaotic 3D parity: droplet-laden forced isotropic turbulence, the recipe of
+the 512^3 benchmark workload (Sec. IV: periodic cube, D3Q19 + D3Q7,
+conservative Allen-Cahn, density ratio 1, W = 4, linear forcing) at 48^3,
+a size the FP64 oracle runs in a test.
+
+The flow is chaotic, so pointwise parity ends after a finite horizon. The
+bars are the ones for the turbulent cases: the time series of the droplet
+volume (the Sec. IV A count of cells with phi > phi_0) and of the kinetic
+energy within 1 % of the oracle's, and conservation of sum(phi) (and with
+it of the smooth volume, Eq. volume_continuous). The horizon where the FP32
+and FP64 fields part is measured here (relative L-infinity of u and phi at
+checkpoints) and printed with the series errors; the series bars are
+asserted up to that horizon and reported beyond it.
+
+Inputs: single-phase turbulence spun up from the seeded random solenoidal
+field by cases.spun_up_turbulence (a pseudo-spectral solver with linear
+forcing held at constant energy; Re_lambda is printed), then two droplets of
+R = 10 at seeded uniform-random positions, sigma = rho u'^2 (2R)/We for
+We in {5, 20}, and the constant forcing coefficient that held the spun-up
+flow stationary; 800 steps. The oracle runs (tests/long_jobs.py) start in
+spawned processes when the session begins and overlap with the GPU runs.
+"""
+
+import numpy as np
+import pytest
+
+from paper_2511_11360_gb300 import pflb
+
+import long_jobs as L
+from gpu_common import record, rel_linf, require_gpu, torch  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+N = L.TURB_N
+NSTEPS = L.TURB_STEPS
+CHECKS = L.TURB_CHECKS
+WES = L.TURB_WES
+
+
+class _Oracle:
+    def __init__(self):
+        self.cache = {}
+
+    def __getitem__(self, We):
+        if We not in self.cache:
+            self.cache[We] = L.result(("turb", We))
+        return self.cache[We]
+
+
+@pytest.fixture(scope="module")
+def hit48():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    L.start()
+    P, phi32, u32, stats = L.turbulence_inputs()
+    require_gpu()
+    print("spun-up turbulence %d^3: Re_lambda %.1f, u' %.4f, eps %.3e, eta %.2f, A %.3e; "
+          "droplet volume fraction %.3f" % (N, stats["Re_lambda"], stats["u_prime"], stats["eps"], stats["eta"],
+                                             stats["A"], float((phi32 > 0.5).mean())))
+    return dict(P=P, phi=phi32, u=u32, oracle=_Oracle(), stats=stats)
+
+
+def gpu_run(P, phi, u, storage=0):
+    """GPU trajectory: per-step observables (steps 0..NSTEPS) and phi, u at
+    the checkpoints."""
+    sim = pflb.Sim(dict(P, storage=storage, obs_capacity=NSTEPS + 8))
+    sim.init(phi, u)
+    fields = {}
+    done = 0
+    for c in CHECKS:
+        sim.step(c - done)
+        done = c
+        ph, uu, _ = sim.fields()
+        fields[c] = (ph, uu)
+    hist = sim.history(NSTEPS) + [sim.observables()]
+    sim.close()
+    assert [h["step"] for h in hist] == list(range(NSTEPS + 1))
+    assert all(h["status"] == 0 for h in hist)
+    s = {k: np.array([h[k] for h in hist], dtype=np.float64) for k in ("sum_phi", "vol_smooth", "vol_count", "ke")}
+    return s, fields
+
+
+def series_errors(gs, os_, steps):
+    """Relative differences of the GPU series gs (every step) from os_ at the
+    oracle's sampled steps: KE against KE(t), the count against its t = 0
+    value."""
+    ke = np.abs(gs["ke"][steps] - os_["ke"]) / os_["ke"]
+    vc = np.abs(gs["vol_count"][steps] - os_["vol_count"]) / os_["vol_count"][0]
+    return ke, vc
+
+
+@pytest.mark.parametrize("We", WES, ids=["We5", "We20"])
+def test_hit48_fp32_series_vs_oracle(hit48, We):
+    P = hit48["P"][We]
+    gs, gf = gpu_run(P, hit48["phi"], hit48["u"])
+    os_, of = hit48["oracle"][We]
+    steps = os_["step"]
+    # Pointwise divergence of the FP32 and FP64 trajectories, and its horizon.
+    div = [(c, rel_linf(gf[c][0], of[c][0]), rel_linf(gf[c][1], of[c][1])) for c in CHECKS]
+    horizon = next((c for c, _, eu in div if eu > 1e-2), None)
+    lim = NSTEPS if horizon is None else horizon
+    ke, vc = series_errors(gs, os_, steps)
+    inside = steps <= lim
+    print("We %g: pointwise rel Linf (step, phi, u): %s" % (We, ", ".join("(%d %.1e %.1e)" % d for d in div)))
+    print("We %g: fields part (u > 1e-2) at step %s; KE series max rel err %.2e, V_count %.2e up to step %d; "
+          "over all %d steps KE %.2e, V_count %.2e; V_count %d -> %d, KE %.4e -> %.4e" % (
+              We, horizon if horizon is not None else ">%d" % NSTEPS, ke[inside].max(), vc[inside].max(), lim,
+              NSTEPS, ke.max(), vc.max(), os_["vol_count"][0], os_["vol_count"][-1], os_["ke"][0], os_["ke"][-1]))
+    drift_g = float(np.max(np.abs(gs["sum_phi"] / gs["sum_phi"][0] - 1)))
+    drift_o = float(np.max(np.abs(os_["sum_phi"] / os_["sum_phi"][0] - 1)))
+    vs_g = float(np.max(np.abs(gs["vol_smooth"] / gs["vol_smooth"][0] - 1)))
+    record("series", We=We, Re_lambda=hit48["stats"]["Re_lambda"], horizon=horizon,
+           ke_max=float(ke[inside].max()), vcount_max=float(vc[inside].max()),
+           ke_all=float(ke.max()), vcount_all=float(vc.max()), sum_phi_drift_gpu=drift_g,
+           sum_phi_drift_oracle=drift_o, divergence=div)
+    assert ke[inside].max() <= 1e-2
+    assert vc[inside].max() <= 1e-2
+    # conservation: sum(phi) and the smooth volume
+    assert drift_o <= 1e-12
+    assert drift_g <= 1e-6 and vs_g <= 1e-6
+
+
+STORAGE_SERIES_BOUND = {1: 5e-2, 2: 5e-2}
+
+
+@pytest.mark.parametrize("storage", [1, 2], ids=["fp16", "bf16"])
+def test_hit48_16bit_series(hit48, storage):
+    """FP16 / BF16 deviation storage on the same case (We = 5): the KE and
+    volume series against the FP32 GPU run and against the FP64 oracle, and
+    the sum(phi) drift the 16-bit rounding causes; bounds are the measured
+    errors with margin."""
+    We = 5.0
+    P = hit48["P"][We]
+    g32, _ = gpu_run(P, hit48["phi"], hit48["u"])
+    g16, _ = gpu_run(P, hit48["phi"], hit48["u"], storage=storage)
+    os_, _ = hit48["oracle"][We]
+    steps = os_["step"]
+    ke_o, vc_o = series_errors(g16, os_, steps)
+    ke_32 = np.abs(g16["ke"] - g32["ke"]) / g32["ke"]
+    vc_32 = np.abs(g16["vol_count"] - g32["vol_count"]) / g32["vol_count"][0]
+    drift = float(np.max(np.abs(g16["sum_phi"] / g16["sum_phi"][0] - 1)))
+    name = {1: "fp16", 2: "bf16"}[storage]
+    print("%s: vs FP32 KE %.2e V_count %.2e; vs FP64 oracle KE %.2e V_count %.2e; sum phi drift %.2e "
+          "over %d steps" % (name, ke_32.max(), vc_32.max(), ke_o.max(), vc_o.max(), drift, NSTEPS))
+    record("series16", storage=name, ke_vs_fp32=float(ke_32.max()), vcount_vs_fp32=float(vc_32.max()),
+           ke_vs_oracle=float(ke_o.max()), vcount_vs_oracle=float(vc_o.max()), sum_phi_drift=drift)
+    b = STORAGE_SERIES_BOUND[storage]
+    assert ke_o.max() <= b and vc_o.max() <= b
