@@ -229,7 +229,7 @@ def e2e_run(P, phi_host, u_host, steps, world):
 def batched_variant(steps, warmup, peak, count=512):
     """The batched sweep: ``count`` moving-wall channels with a droplet, L
     uniform in {64, 128, 256, 512}, Ca ~ U[0.05, 0.5], M ~ U[0.01, 0.2],
-    W in {3, 4, 5}, family uniform over the four; FP32; one persistent launch
+    W in {3, 4, 5}, family uniform over the five fused-step families; FP32; one persistent launch
     per step (plus the gamma pre-pass when nonlocal domains are present),
     launch shape from the autotuner, steps replayed as CUDA graphs."""
     import numpy as np
@@ -262,13 +262,14 @@ def batched_variant(steps, warmup, peak, count=512):
         status = str(ex)
     cells, nbytes = b.cells(), b.bytes_per_step()
     b.close()
-    fams = [0, 0, 0, 0]
+    fams = [0, 0, 0, 0, 0]
     for s in specs:
         fams[s["family"]] += 1
     return {"value": cells * steps / t / 1e9, "unit": "GLUPS", "instances": count, "cells": cells,
             "bytes_per_lu": nbytes / cells, "roofline_frac": nbytes / (t / steps) / 1e9 / peak,
             "ms_per_step": t / steps * 1e3, "launch": tune, "graph": True,
-            "families": {"fakhari2017": fams[0], "chai2018": fams[1], "hu2019": fams[2], "liang2014": fams[3]},
+            "families": {"fakhari2017": fams[0], "chai2018": fams[1], "hu2019": fams[2], "liang2014": fams[3],
+                         "liang2018": fams[4]},
             "status": status,
             "err_vs_oracle": "each domain bitwise the single-domain step (nonlocal gamma: FP64 sum order); "
                              "sampled domains vs FP64 oracle as the 2D fp32 path (tests/test_gpu_batch.py)"}
@@ -425,10 +426,22 @@ def oracle_on_host_cores(n, warmup, steps, cores=None):
     cores = cores or os.cpu_count() or 1
     ctx = multiprocessing.get_context("spawn")
     barrier = ctx.Barrier(cores)
-    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=ctx, initializer=_oracle_worker_init,
-                                initargs=(barrier,)) as ex:
-        times = list(ex.map(_oracle_sample_run, [n] * cores, [warmup] * cores, [steps] * cores,
-                            [20251114 + k for k in range(cores)]))
+    # one thread per process: the workers inherit these before numpy loads
+    # (otherwise each process's BLAS starts a thread per core)
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        with cf.ProcessPoolExecutor(max_workers=cores, mp_context=ctx, initializer=_oracle_worker_init,
+                                    initargs=(barrier,)) as ex:
+            times = list(ex.map(_oracle_sample_run, [n] * cores, [warmup] * cores, [steps] * cores,
+                                [20251114 + k for k in range(cores)]))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
     t = max(times)
     return cores * n ** 3 * steps / t / 1e9, cores, t
 
@@ -480,8 +493,9 @@ def main():
     ap.add_argument("--family", default="fakhari2017",
                     choices=["fakhari2017", "chai2018", "hu2019", "liang2014", "liang2018", "bao2024", "liu2023"],
                     help="phase-field family of the primary leg (the headline is fakhari2017)")
-    ap.add_argument("--staging", type=int, default=1, choices=[0, 1],
-                    help="1: TMA staging of the populations (default, where the geometry allows); 0: cp.async")
+    ap.add_argument("--staging", type=int, default=2, choices=[0, 1, 2],
+                    help="staging of the populations: 0 cp.async, 1 TMA where the geometry allows, "
+                         "2 (default) TMA for FP32 storage only")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
@@ -546,7 +560,7 @@ def main():
         # tensor copies or per-thread cp.async), identical results
         s1 = pflb.Sim(dict(P, storage=storage, obs_capacity=4), stream=torch.cuda.current_stream())
         s1.init(phi, u)
-        s1.set_staging(1 - args.staging)
+        s1.set_staging(0 if sim.staging == 1 else 1)
         other = "tma" if s1.staging == 1 else "cp.async"
         if other != staging:
             t1 = _max_over_ranks(time_steps(s1, args.steps, args.warmup, world), world)

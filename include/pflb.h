@@ -214,15 +214,21 @@ double pflb_bytes_per_update(const pflb_handle* h);
 int pflb_set_chunk(pflb_handle* h, int32_t chunk);
 
 /* How the fused 3D step stages each plane's populations in shared memory.
- * mode 1 (the default): tensor-memory-accelerator bulk copies of boxes of
- * the population arrays (a 5-D view: lane, slot, 32-cell x-block, y, z),
- * completed on shared-memory barriers whose waits are bounded -- used where
- * the domain is 3D, nx is a multiple of 32, ny a multiple of the tile's rows
- * (4) and at least 8, and the family is Fakhari2017, Chai2018, Hu2019 or
- * Liang2018; elsewhere mode 1 falls back to mode 0. mode 0: per-thread
- * cp.async copies. Both compute bit-identical results (Sec. II B and the
- * streaming of this header's conventions are unchanged). PFLB_EINVAL for
- * another mode. */
+ * TMA staging: tensor-memory-accelerator bulk copies of boxes of the
+ * population arrays (a 5-D view: lane, slot, 32-cell x-block, y, z),
+ * completed on shared-memory barriers whose waits are bounded; available
+ * where the domain is 3D, nx is a multiple of 32, ny a multiple of the
+ * tile's rows (4) and at least 8, and the family is Fakhari2017, Chai2018,
+ * Hu2019 or Liang2018. cp.async staging: per-thread asynchronous copies.
+ *   mode 0: cp.async staging everywhere;
+ *   mode 1: TMA staging where available;
+ *   mode 2 (the default): TMA staging for FP32 storage on D3Q19 where
+ *           available, cp.async for the 16-bit forms (which are bound by
+ *           instruction issue, where the per-thread barrier waits cost more
+ *           than the copies they replace) and for D3Q27 (measured slower
+ *           with TMA at three blocks per SM).
+ * Both stagings compute bit-identical populations. PFLB_EINVAL for another
+ * mode. */
 int pflb_set_staging(pflb_handle* h, int32_t mode);
 
 /* 1 if the next step of h uses TMA staging, 0 if it uses cp.async staging,

@@ -308,14 +308,15 @@ def shear_instance(L, family, Ca, M, W, Uw=0.02, tau=0.8):
 
 def batched_shear_sweep(count=512, sizes=(64, 128, 256, 512), seed=DEFAULT_SEED):
     """``count`` instances with L uniform in ``sizes``, Ca ~ U[0.05, 0.5],
-    M ~ U[0.01, 0.2], W uniform in {3, 4, 5}, family uniform over the four
-    families of the paper's model comparison (Fakhari2017, Chai2018, Hu2019,
-    Liang2014)."""
+    M ~ U[0.01, 0.2], W uniform in {3, 4, 5}, family uniform over the five
+    families of the fused step (Fakhari2017, Chai2018, Hu2019, Liang2014,
+    Liang2018: the four categories of the paper's comparison and its second
+    conservative Allen-Cahn model)."""
     rng = np.random.default_rng(seed)
     out = []
     for _ in range(count):
         L = int(rng.choice(sizes))
-        fam = int(rng.integers(0, 4))
+        fam = int(rng.integers(0, 5))
         Ca = float(rng.uniform(0.05, 0.5))
         M = float(rng.uniform(0.01, 0.2))
         W = int(rng.choice([3, 4, 5]))

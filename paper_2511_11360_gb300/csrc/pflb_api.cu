@@ -233,7 +233,7 @@ StepArgs pflb::handle_step_args(const pflb_handle* h) {
   a.parity = (int)(h->step & 1);
   a.chunk = h->chunk > 0 ? h->chunk : default_chunk(h);
   a.N = h->N;
-  a.tma = h->staging == 1 ? h->tma[h->cur] : nullptr;
+  a.tma = (h->staging == 1 || (h->staging == 2 && h->storage == 0 && h->QF == 19)) ? h->tma[h->cur] : nullptr;
   a.seed = (unsigned)h->step;
   return a;
 }

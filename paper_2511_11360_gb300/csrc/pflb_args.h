@@ -93,7 +93,7 @@ struct BatchGammaEntry {
 
 struct BatchArgs {
   const StepArgs* args;     // per instance: this step's arguments
-  const BatchTile* tiles;
+  const BatchTile* tiles;   // this family's tiles
   int ntiles;
   int ninst;
   int chunk;                // rows per tile along y
@@ -128,8 +128,8 @@ void gamma_sums(int dim, int storage, const GammaArgs& a, cudaStream_t s);
 void canon_copy(int dim, int storage, const CanonArgs& a, cudaStream_t s);
 // pflb_batch_kernels.cu (2D, FP32 storage)
 bool batch_tile_supported(int tile_a);
-int batch_max_blocks_per_sm(int tile_a);
-void batch_step(int tile_a, const BatchArgs& a, int grid, cudaStream_t s);
+int batch_max_blocks_per_sm(int tile_a, int fam);
+void batch_step(int tile_a, int fam, const BatchArgs& a, int grid, cudaStream_t s);
 void batch_gamma(const BatchGammaArgs& a, int grid, cudaStream_t s);
 void batch_obs_gather(const DevObs* const* src, DevObs* dst, int n, cudaStream_t s);
 

@@ -14,20 +14,27 @@
 
 using namespace pflb;
 
+constexpr int kBatchFams = 5;   // the fused-step families 0..4
+
 struct pflb_batch {
   std::vector<pflb_handle*> dom;
   cudaStream_t stream = nullptr;   // the caller's stream (every domain's)
   cudaStream_t gstream = nullptr;  // internal stream the graphs replay on
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   pflb_batch_launch cfg = {128, 16, 0, 0, 0.0};
-  int grid = 0;                    // persistent blocks of the step kernel
+  int grid = 0;                    // resident blocks the launch shape allows (every family's kernel)
+  int fam_t0[kBatchFams] = {};      // the families' ranges of the tile list
+  int fam_n[kBatchFams] = {};
+  int fgrid[kBatchFams] = {};       // persistent blocks of each family's kernel
+  cudaStream_t fstream[kBatchFams] = {};   // branches of a step (the first family runs on the step's stream)
+  cudaEvent_t ev_fork = nullptr, ev_join[kBatchFams] = {};
   int ggrid = 0;                   // blocks of the gamma pre-pass
   BatchTile* d_tiles = nullptr;
   int ntiles = 0;
   BatchGammaEntry* d_gent = nullptr;
   int ngent = 0;
   StepArgs* d_args = nullptr;      // 2 x n: arguments of the next step and the one after
-  unsigned* d_counter = nullptr;   // tile claim counters of those two steps
+  unsigned* d_counter = nullptr;   // tile claim counters of those two steps, one per family
   DevObs** d_obs_src = nullptr;
   DevObs* d_obs_out = nullptr;
   bool layout_ok = false, tables_ok = false;
@@ -114,13 +121,22 @@ int build_layout(pflb_batch* b) {
   if ((rc = upload(b, &b->d_gent, gent))) return rc;
   b->ntiles = (int)tiles.size();
   b->ngent = (int)gent.size();
+  for (int f = 0; f < kBatchFams; ++f) b->fam_t0[f] = b->fam_n[f] = 0;
+  for (int t = 0; t < b->ntiles; ++t) {
+    const int f = tiles[t].fam;
+    if (b->fam_n[f]++ == 0) b->fam_t0[f] = t;
+  }
   const int sms = num_sms();
-  const int maxb = batch_max_blocks_per_sm(ta);
-  int bps = b->cfg.blocks_per_sm > 0 ? b->cfg.blocks_per_sm : maxb;
-  if (bps > maxb) bps = maxb;
-  long long grid = (long long)bps * sms;
-  if (grid > b->ntiles) grid = b->ntiles > 0 ? b->ntiles : 1;
-  b->grid = (int)grid;
+  b->grid = 0;
+  for (int f = 0; f < kBatchFams; ++f) {
+    const int maxb = batch_max_blocks_per_sm(ta, f);
+    int bps = b->cfg.blocks_per_sm > 0 ? b->cfg.blocks_per_sm : maxb;
+    if (bps > maxb) bps = maxb;
+    long long grid = (long long)bps * sms;
+    if (grid > b->fam_n[f]) grid = b->fam_n[f];
+    b->fgrid[f] = (int)grid;
+    if (b->fgrid[f] > b->grid) b->grid = b->fgrid[f];
+  }
   b->ggrid = b->ngent < 4 * sms ? (b->ngent > 0 ? b->ngent : 1) : 4 * sms;
   drop_graphs(b);
   b->layout_ok = true;
@@ -158,7 +174,7 @@ int build_tables(pflb_batch* b) {
     b->exp_cur[i] = b->dom[i]->cur;
   }
   BCU(b, cudaMemcpyAsync(b->d_args, t.data(), t.size() * sizeof(StepArgs), cudaMemcpyHostToDevice, b->stream));
-  BCU(b, cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(unsigned), b->stream));
+  BCU(b, cudaMemsetAsync(b->d_counter, 0, 2 * kBatchFams * sizeof(unsigned), b->stream));
   BCU(b, cudaStreamSynchronize(b->stream));
   b->ph = 0;
   b->tables_ok = true;
@@ -181,7 +197,9 @@ int prepare(pflb_batch* b) {
   return PFLB_OK;
 }
 
-// One batched step using argument table k, on stream s.
+// One batched step using argument table k, on stream s: the gamma pre-pass,
+// then one kernel per family present, forked on the family streams after the
+// pre-pass and joined back into s (the same dependencies in a captured graph).
 void launch_one(pflb_batch* b, int k, cudaStream_t s) {
   const int n = n_of(b);
   if (b->ngent > 0) {
@@ -192,15 +210,27 @@ void launch_one(pflb_batch* b, int k, cudaStream_t s) {
     ga.ninst = n;
     batch_gamma(ga, b->ggrid, s);
   }
-  BatchArgs ba;
-  ba.args = b->d_args + (size_t)k * n;
-  ba.tiles = b->d_tiles;
-  ba.ntiles = b->ntiles;
-  ba.ninst = n;
-  ba.chunk = b->cfg.chunk;
-  ba.counter = b->d_counter + k;
-  ba.counter_next = b->d_counter + (1 - k);
-  batch_step(b->cfg.tile_a, ba, b->grid, s);
+  bool first = true;
+  cudaEventRecord(b->ev_fork, s);
+  for (int f = 0; f < kBatchFams; ++f) {
+    if (b->fam_n[f] == 0) continue;
+    BatchArgs ba;
+    ba.args = b->d_args + (size_t)k * n;
+    ba.tiles = b->d_tiles + b->fam_t0[f];
+    ba.ntiles = b->fam_n[f];
+    ba.ninst = n;
+    ba.chunk = b->cfg.chunk;
+    ba.counter = b->d_counter + k * kBatchFams + f;
+    ba.counter_next = b->d_counter + (1 - k) * kBatchFams + f;
+    cudaStream_t sf = first ? s : b->fstream[f];
+    if (!first) cudaStreamWaitEvent(sf, b->ev_fork, 0);
+    batch_step(b->cfg.tile_a, f, ba, b->fgrid[f], sf);
+    if (!first) {
+      cudaEventRecord(b->ev_join[f], sf);
+      cudaStreamWaitEvent(s, b->ev_join[f], 0);
+    }
+    first = false;
+  }
 }
 
 int capture_graphs(pflb_batch* b) {
@@ -480,6 +510,11 @@ int pflb_batch_create(const pflb_params* params, int32_t n, void* cuda_stream, p
   BCU(b, cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking));
   BCU(b, cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
   BCU(b, cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
+  BCU(b, cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+  for (int f = 0; f < kBatchFams; ++f) {
+    BCU(b, cudaStreamCreateWithFlags(&b->fstream[f], cudaStreamNonBlocking));
+    BCU(b, cudaEventCreateWithFlags(&b->ev_join[f], cudaEventDisableTiming));
+  }
   auto alloc = [&](void** p, size_t bytes) -> int {
     if (cudaMalloc(p, bytes) != cudaSuccess) {
       cudaGetLastError();
@@ -489,10 +524,10 @@ int pflb_batch_create(const pflb_params* params, int32_t n, void* cuda_stream, p
   };
   int rc;
   if ((rc = alloc((void**)&b->d_args, 2 * (size_t)n * sizeof(StepArgs)))) return rc;
-  if ((rc = alloc((void**)&b->d_counter, 2 * sizeof(unsigned)))) return rc;
+  if ((rc = alloc((void**)&b->d_counter, 2 * kBatchFams * sizeof(unsigned)))) return rc;
   if ((rc = alloc((void**)&b->d_obs_src, (size_t)n * sizeof(DevObs*)))) return rc;
   if ((rc = alloc((void**)&b->d_obs_out, (size_t)n * sizeof(DevObs)))) return rc;
-  BCU(b, cudaMemset(b->d_counter, 0, 2 * sizeof(unsigned)));
+  BCU(b, cudaMemset(b->d_counter, 0, 2 * kBatchFams * sizeof(unsigned)));
   return PFLB_OK;
 }
 
@@ -561,7 +596,9 @@ int pflb_batch_autotune(pflb_batch* b, int32_t steps_per_trial, const char* cach
   static const int tas[3] = {64, 128, 256};
   static const int chunks[4] = {8, 16, 32, 64};
   for (int ta : tas) {
-    const int maxb = batch_max_blocks_per_sm(ta);
+    int maxb = 1;
+    for (int f = 0; f < kBatchFams; ++f)
+      maxb = batch_max_blocks_per_sm(ta, f) > maxb ? batch_max_blocks_per_sm(ta, f) : maxb;
     const int bpss[2] = {0, maxb / 2};
     for (int ci = 0; ci < 4 && rc == PFLB_OK; ++ci) {
       for (int bi = 0; bi < 2 && rc == PFLB_OK; ++bi) {
@@ -634,6 +671,14 @@ int pflb_batch_destroy(pflb_batch* b) {
   drop_graphs(b);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
+  for (int f = 0; f < kBatchFams; ++f) {
+    if (b->fstream[f]) {
+      cudaStreamSynchronize(b->fstream[f]);
+      cudaStreamDestroy(b->fstream[f]);
+    }
+    if (b->ev_join[f]) cudaEventDestroy(b->ev_join[f]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   if (b->gstream) cudaStreamDestroy(b->gstream);
   cudaFree(b->d_tiles);
   cudaFree(b->d_gent);

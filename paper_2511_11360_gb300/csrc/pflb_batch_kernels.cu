@@ -1,9 +1,9 @@
 // Kernels of the batched step: many 2D domains of uneven size, family and
-// parameters advanced by one persistent launch (FP32 storage).
+// parameters advanced by one persistent launch per family (FP32 storage).
 //
-// The tile work list holds every (domain, x-tile, y-chunk) of the batch.
-// Resident blocks claim tiles from an atomic counter until the list is
-// exhausted; each tile runs the same per-cell update as the single-domain
+// The tile work list holds every (domain, x-tile, y-chunk) of the batch,
+// grouped by family. Resident blocks claim tiles of their family from an
+// atomic counter until that range is exhausted; each tile runs the same per-cell update as the single-domain
 // kernel (step_tile), so a domain advanced in a batch is bitwise identical
 // to the same domain advanced alone (its observables differ only in the
 // order of the FP64 sums). The counter of the next step is reset by the
@@ -19,9 +19,15 @@ struct BatchGeom {
   static constexpr int MINB = 512 / TA;
 };
 
-template <int TA>
+// One family's tiles: the resident blocks of this kernel claim the tiles of
+// one family (a contiguous range of the work list) from that family's
+// counter, so each kernel holds one family's code and shared-memory
+// footprint. The families' kernels of one step run as concurrent branches
+// (the host forks them on separate streams), so one family's last tiles
+// overlap the next family's first ones.
+template <int TA, int FAM>
 __global__ void __launch_bounds__(TA, BatchGeom<TA>::MINB) batch_step_kernel(const BatchArgs ba) {
-  using SMX = TileSmem<FAM_LIANG, 2, float, TA, 1>;  // the largest footprint of the families
+  using SMX = TileSmem<FAM, 2, float, TA, 1>;
   extern __shared__ __align__(16) float dyn_smem[];
   float* s_stage = dyn_smem;
   float* s_phi = dyn_smem + SMX::STAGE;
@@ -33,9 +39,10 @@ __global__ void __launch_bounds__(TA, BatchGeom<TA>::MINB) batch_step_kernel(con
   const int tid = threadIdx.x;
 
   if (blockIdx.x == 0 && tid == 0) *ba.counter_next = 0u;
+  // the next step's observables slot of this family's domains
   for (int i = blockIdx.x * TA + tid; i < ba.ninst; i += gridDim.x * TA) {
     DevObs* z = ba.args[i].obs_zero;
-    if (z != nullptr) obs_zero_slot(z);
+    if (z != nullptr && ba.args[i].p.family == FAM) obs_zero_slot(z);
   }
 
   for (;;) {
@@ -54,39 +61,10 @@ __global__ void __launch_bounds__(TA, BatchGeom<TA>::MINB) batch_step_kernel(con
     obs_init(obs);
     // Widths that are a multiple of the population block take the
     // constant-offset addressing (the sweep's widths all are).
-    const bool row = s_args.p.nx % (int)kPopBlock == 0;
-    switch (e.fam * 2 + (row ? 1 : 0)) {
-      case 2 * FAM_FAKHARI + 1:
-        step_tile<FAM_FAKHARI, 2, float, TA, 1, -1, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
-        break;
-      case 2 * FAM_FAKHARI:
-        step_tile<FAM_FAKHARI, 2, float, TA, 1, -1, 0>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
-        break;
-      case 2 * FAM_CHAI + 1:
-        step_tile<FAM_CHAI, 2, float, TA, 1, -1, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
-        break;
-      case 2 * FAM_CHAI:
-        step_tile<FAM_CHAI, 2, float, TA, 1, -1, 0>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
-        break;
-      case 2 * FAM_HU + 1:
-        step_tile<FAM_HU, 2, float, TA, 1, -1, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
-        break;
-      case 2 * FAM_HU:
-        step_tile<FAM_HU, 2, float, TA, 1, -1, 0>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
-        break;
-      case 2 * FAM_LIANG + 1:
-        step_tile<FAM_LIANG, 2, float, TA, 1, -1, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
-        break;
-      case 2 * FAM_LIANG:
-        step_tile<FAM_LIANG, 2, float, TA, 1, -1, 0>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
-        break;
-      case 2 * FAM_LIANG18 + 1:
-        step_tile<FAM_LIANG18, 2, float, TA, 1, -1, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
-        break;
-      default:
-        step_tile<FAM_LIANG18, 2, float, TA, 1, -1, 0>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
-        break;
-    }
+    if (s_args.p.nx % (int)kPopBlock == 0)
+      step_tile<FAM, 2, float, TA, 1, -1, 1>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
+    else
+      step_tile<FAM, 2, float, TA, 1, -1, 0>(s_args, e.a0, 0, e.c0, ba.chunk, s_phi, s_mu, s_stage, obs);
     obs_block_commit(obs, s_args.obs_slot, s_red);
     __syncthreads();  // s_tile, s_args and the rings are rewritten by the next tile
   }
@@ -150,38 +128,63 @@ __global__ void obs_gather_kernel(const DevObs* const* src, DevObs* dst, int n) 
 
 bool batch_tile_supported(int tile_a) { return tile_a == 64 || tile_a == 128 || tile_a == 256; }
 
-template <int TA>
+template <int TA, int FAM>
 static size_t batch_smem() {
-  constexpr size_t smem = TileSmem<FAM_LIANG, 2, float, TA, 1>::BYTES;
+  constexpr size_t smem = TileSmem<FAM, 2, float, TA, 1>::BYTES;
   static const cudaError_t attr =
-      cudaFuncSetAttribute(batch_step_kernel<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(batch_step_kernel<TA, FAM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   (void)attr;
   return smem;
 }
 
-template <int TA>
+template <int TA, int FAM>
 static int max_blocks() {
   int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_step_kernel<TA>, TA, batch_smem<TA>()) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_step_kernel<TA, FAM>, TA, batch_smem<TA, FAM>()) !=
+      cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
   return b > 0 ? b : 1;
 }
 
-int batch_max_blocks_per_sm(int tile_a) {
-  switch (tile_a) {
-    case 64: return max_blocks<64>();
-    case 128: return max_blocks<128>();
-    default: return max_blocks<256>();
+template <int TA>
+static int max_blocks_ta(int fam) {
+  switch (fam) {
+    case FAM_FAKHARI: return max_blocks<TA, FAM_FAKHARI>();
+    case FAM_CHAI: return max_blocks<TA, FAM_CHAI>();
+    case FAM_HU: return max_blocks<TA, FAM_HU>();
+    case FAM_LIANG: return max_blocks<TA, FAM_LIANG>();
+    default: return max_blocks<TA, FAM_LIANG18>();
   }
 }
 
-void batch_step(int tile_a, const BatchArgs& a, int grid, cudaStream_t s) {
+int batch_max_blocks_per_sm(int tile_a, int fam) {
   switch (tile_a) {
-    case 64: batch_step_kernel<64><<<grid, 64, batch_smem<64>(), s>>>(a); break;
-    case 128: batch_step_kernel<128><<<grid, 128, batch_smem<128>(), s>>>(a); break;
-    default: batch_step_kernel<256><<<grid, 256, batch_smem<256>(), s>>>(a); break;
+    case 64: return max_blocks_ta<64>(fam);
+    case 128: return max_blocks_ta<128>(fam);
+    default: return max_blocks_ta<256>(fam);
+  }
+}
+
+template <int TA>
+static void step_ta(int fam, const BatchArgs& a, int grid, cudaStream_t s) {
+  switch (fam) {
+    case FAM_FAKHARI:
+      batch_step_kernel<TA, FAM_FAKHARI><<<grid, TA, batch_smem<TA, FAM_FAKHARI>(), s>>>(a);
+      break;
+    case FAM_CHAI: batch_step_kernel<TA, FAM_CHAI><<<grid, TA, batch_smem<TA, FAM_CHAI>(), s>>>(a); break;
+    case FAM_HU: batch_step_kernel<TA, FAM_HU><<<grid, TA, batch_smem<TA, FAM_HU>(), s>>>(a); break;
+    case FAM_LIANG: batch_step_kernel<TA, FAM_LIANG><<<grid, TA, batch_smem<TA, FAM_LIANG>(), s>>>(a); break;
+    default: batch_step_kernel<TA, FAM_LIANG18><<<grid, TA, batch_smem<TA, FAM_LIANG18>(), s>>>(a); break;
+  }
+}
+
+void batch_step(int tile_a, int fam, const BatchArgs& a, int grid, cudaStream_t s) {
+  switch (tile_a) {
+    case 64: step_ta<64>(fam, a, grid, s); break;
+    case 128: step_ta<128>(fam, a, grid, s); break;
+    default: step_ta<256>(fam, a, grid, s); break;
   }
 }
 

@@ -242,24 +242,19 @@ __host__ __device__ constexpr float pow2_scale(int a) {
 // value that repeats step after step (quasi-steady regions) repeats its
 // error, and the errors add up coherently -- linearly in the step count,
 // and in the sum of phi, which the populations carry. Rounding up with
-// probability equal to the dropped fraction makes each error zero-mean and
-// independent, so they add up as a random walk. The random bits come from a
-// counter-based stream per cell and step: a 32-bit integer hash of (cell,
-// step) seeds it, a 32-bit linear congruential step advances it per store,
-// and its top bits are used. The result depends only on (cell, step), not on
-// the launch shape.
+// probability equal to the dropped fraction makes each error zero-mean, so
+// they add up as a random walk. The random threshold comes from a
+// counter-based integer hash of (cell, step), one per cell and step, shared
+// by that cell's stores: every store is still unbiased, and the g that
+// meet at a cell after push streaming come from different cells, so their
+// thresholds are independent where phi sums them. The result depends only
+// on (cell, step), not on the launch shape or the staging.
 __device__ __forceinline__ unsigned dither_seed(unsigned cell, unsigned step) {
-  unsigned x = cell * 0x9E3779B9u ^ (step * 0x85EBCA6Bu + 0x2545F491u);
-  x ^= x >> 16;
-  x *= 0x7FEB352Du;
+  unsigned x = (cell ^ (step * 0x85EBCA6Bu)) * 0x9E3779B9u;
   x ^= x >> 15;
-  x *= 0x846CA68Bu;
-  x ^= x >> 16;
+  x *= 0x2C1B3C6Du;
+  x ^= x >> 12;
   return x;
-}
-__device__ __forceinline__ unsigned dither_next(unsigned& s) {
-  s = s * 1664525u + 1013904223u;
-  return s;
 }
 
 template <typename T> struct Codec;
@@ -359,14 +354,14 @@ template <typename T, typename L>
 __device__ __forceinline__ void pop_store(T* p, int q, float v, float c) {
   Codec<T>::st(p, v, 1.0f / pow2_scale<L>(q), wprime<L>(q) * c);
 }
-// The per-step store: stochastically rounded in 16-bit storage (the dither
-// stream rng advances once per store), exact in FP32.
+// The per-step store: stochastically rounded in 16-bit storage with the
+// cell's threshold r (dither_seed), exact in FP32.
 template <typename T, typename L>
-__device__ __forceinline__ void pop_store_sr(T* p, int q, float v, float c, unsigned& rng) {
+__device__ __forceinline__ void pop_store_sr(T* p, int q, float v, float c, unsigned r) {
   if constexpr (std::is_same<T, float>::value) {
     *p = v;
   } else {
-    Codec<T>::st_sr(p, v, 1.0f / pow2_scale<L>(q), wprime<L>(q) * c, dither_next(rng));
+    Codec<T>::st_sr(p, v, 1.0f / pow2_scale<L>(q), wprime<L>(q) * c, r);
   }
 }
 

@@ -27,7 +27,7 @@ struct pflb_handle {
   int status = PFLB_OK;
   char err[512] = {0};
   pflb::TmaMaps* tma[2] = {nullptr, nullptr};  // tensor maps per g source buffer (TMA staging), or null
-  int staging = 1;              // 1: TMA staging where the geometry allows it; 0: cp.async staging
+  int staging = 2;              // 0 cp.async staging; 1 TMA where the geometry allows it; 2 TMA for FP32 D3Q19 only
 };
 
 namespace pflb {

@@ -277,6 +277,20 @@ struct Cell {
         geq[0] = phi - Sym<LG>::moving(geq);
         if constexpr (FAM == FAM_CHAI || FAM == FAM_HU || FAM == FAM_LIU) G[0] = wmul<LG>(0, Rw);
       }
+      if constexpr (FAM == FAM_FAKHARI && QG == 7) {
+        // D3Q7 has no rest population to absorb the rounding of the
+        // second-order equilibrium (w_0 = 0), and the FP32 terms
+        // 4.5 (e.u)^2 - 1.5 u.u of the six did not sum to zero: phi drifted
+        // by ~3e-9 per step. The z pair takes the even part that makes the
+        // six sum to phi (one rounding), h = (phi - x and y pairs) / 2, and
+        // keeps its odd part w phi 3 u_z; exact arithmetic gives the same
+        // values, and every reflection still maps the update onto itself.
+        const float S = (geq[1] + geq[2]) + (geq[3] + geq[4]);
+        const float h = 0.5f * (phi - S);
+        const float o = wmul<LG>(5, phi * (3.0f * u[DIM - 1]));
+        geq[5] = h + o;
+        geq[6] = h - o;
+      }
     }
 #pragma unroll
     for (int q = 0; q < QG; ++q) g[q] = g[q] - (g[q] - geq[q]) * P.inv_tau_phi + P.src_w_phi * G[q];
@@ -1220,7 +1234,7 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
         }
         // g: two-array push, bounce-back into the own cell at walls.
         const float uw_lo = P.moving ? P.wall_u[0] : 0.0f, uw_hi = P.moving ? P.wall_u[1] : 0.0f;
-        unsigned rng = WIDE ? 0u : dither_seed(idx, args.seed);   // 16-bit storage: stochastic rounding
+        const unsigned rng = WIDE ? 0u : dither_seed(idx, args.seed);   // 16-bit storage: stochastic rounding
 #pragma unroll
         for (int q = 0; q < QG; ++q) {
           if (DIM == 3 && !CH && q == 0) continue;

@@ -110,12 +110,13 @@ int handle_build_tma(pflb_handle* h) {
 }  // namespace pflb
 
 int pflb_set_staging(pflb_handle* h, int32_t mode) {
-  if (!h || (mode != 0 && mode != 1)) return pflb::handle_fail(h, PFLB_EINVAL, "staging mode must be 0 or 1");
+  if (!h || mode < 0 || mode > 2) return pflb::handle_fail(h, PFLB_EINVAL, "staging mode must be 0, 1 or 2");
   h->staging = mode;
   return PFLB_OK;
 }
 
 int pflb_get_staging(const pflb_handle* h) {
   if (!h) return PFLB_EINVAL;
-  return (h->staging == 1 && h->tma[h->cur] != nullptr) ? 1 : 0;
+  const bool tma = h->staging == 1 || (h->staging == 2 && h->storage == 0 && h->QF == 19);
+  return (tma && h->tma[h->cur] != nullptr) ? 1 : 0;
 }

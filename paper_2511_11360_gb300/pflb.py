@@ -271,7 +271,8 @@ class Sim:
         return self._check(self.lib.pflb_set_chunk(self.h, int(c)))
 
     def set_staging(self, mode):
-        """1: TMA staging where the geometry allows it (default); 0: cp.async."""
+        """0: cp.async staging; 1: TMA where the geometry allows it; 2 (default):
+        TMA for FP32 storage on D3Q19 only."""
         return self._check(self.lib.pflb_set_staging(self.h, int(mode)))
 
     @property

@@ -49,12 +49,11 @@ def pytest_collection_finish(session):
     oracle runs (tests/long_jobs.py, spawned processes) right after
     collection, so they overlap with the GPU test modules that run first."""
     names = {item.module.__name__ for item in session.items if hasattr(item, "module")}
-    if not ({"test_gpu_rt", "test_gpu_turbulence"} & names):
-        return
-    if not _gpu_session(session):
-        return
     import long_jobs
-    long_jobs.start()
+    groups = [g for g, mod in long_jobs.GROUPS.items() if mod in names]
+    if not groups or not _gpu_session(session):
+        return
+    long_jobs.start(groups)
 
 
 def pytest_sessionfinish(session, exitstatus):

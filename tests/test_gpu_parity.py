@@ -22,7 +22,7 @@ import oracle as O
 from paper_2511_11360_gb300 import cases as C
 from paper_2511_11360_gb300 import pflb
 
-from gpu_common import as_f32, check_parity, compare_fields, make_sim, oracle_start, rel_linf, require_gpu
+from gpu_common import as_f32, check_parity, compare_fields, make_sim, oracle_start, record, rel_linf, require_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -282,24 +282,34 @@ def test_device_buffers_accepted():
 
 
 # ------------------------------------------------------- 16-bit storage error
-@pytest.mark.parametrize("storage,tol", [(1, 5e-2), (2, 1e-1)], ids=["fp16", "bf16"])
-def test_16bit_storage_error_vs_oracle(storage, tol):
-    """FP16/BF16 deviation storage, FP32 arithmetic: error of phi and u against
-    the FP64 oracle after 200 steps of the 3D droplet-in-TGV case. A reported
-    error, not a parity bar: the 16-bit rounding of the stored deviations
-    (relative 2^-11 and 2^-8) repeats deterministically in quasi-steady
-    regions, so it accumulates with the step count."""
+# measured (stochastically rounded stores, deterministic per cell and step):
+# FP16 phi 3.0e-3, u 1.2e-3, sum(phi) drift 2.5e-5; BF16 phi 1.26e-2, u 1.05e-2,
+# drift 2.1e-5 -- the bounds leave a factor 2 (drift: 4)
+BOUND_16 = {1: (6e-3, 3e-3, 1e-4), 2: (2.5e-2, 2.5e-2, 1e-4)}
+
+
+@pytest.mark.parametrize("storage", [1, 2], ids=["fp16", "bf16"])
+def test_16bit_storage_error_vs_oracle(storage):
+    """FP16/BF16 deviation storage, FP32 arithmetic: phi and u against the
+    FP64 oracle after 200 steps of the 3D droplet-in-TGV case, and the drift
+    of sum(phi). Each store rounds stochastically (Reading R11), so the 16-bit
+    rounding errors are zero-mean and add up as a random walk; with
+    round-to-nearest they repeated coherently in quasi-steady regions (phi
+    5.5e-3, u 4.6e-3, drift 5.6e-4 for FP16 on this case)."""
+    b_phi, b_u, b_drift = BOUND_16[storage]
     P, phi, u, chunk = laminar_case("3d", C.FAKHARI2017)
     sim = make_sim(P, phi, u, storage=storage, chunk=chunk)
     sim.step(200)
     st = O.run(P, oracle_start(P, phi, u), 200)
-    e_phi, e_u = compare_fields(sim, P, st, tol, 10 * tol)
-    print("storage %d: phi rel Linf %.3e  u rel Linf %.3e" % (storage, e_phi, e_u))
-    # mass bookkeeping: the 16-bit rounding of the stored deviations breaks
-    # exact conservation; report the drift (FP64 sums of the decoded values)
+    e_phi, e_u = compare_fields(sim, P, st, b_phi, b_u)
     s0 = sim.history(200)[0]["sum_phi"]
     s1 = sim.observables()["sum_phi"]
-    print("storage %d: sum phi drift %.3e over 200 steps" % (storage, s1 / s0 - 1))
+    drift = abs(s1 / s0 - 1)
+    print("storage %d: phi rel Linf %.3e  u rel Linf %.3e  sum phi drift %.3e over 200 steps" % (
+        storage, e_phi, e_u, drift))
+    record("storage16", storage=storage, steps=200, e_phi=e_phi, e_u=e_u, sum_phi_drift=drift,
+           bound_phi=b_phi, bound_u=b_u, bound_drift=b_drift)
+    assert drift <= b_drift
 
 
 # ------------------------------------------------------------- mirror symmetry
@@ -369,6 +379,7 @@ def test_tma_staging_matches_cp_async_bitwise(shape, fam, storage, lat):
         P.update(lattice_f=27, collision=1, mrt_s_bulk=1.1, mrt_s_ho=1.4)
     a = make_sim(P, phi, u, storage=storage, chunk=3)
     b = make_sim(P, phi, u, storage=storage, chunk=3)
+    a.set_staging(1)
     b.set_staging(0)
     assert a.staging == 1 and b.staging == 0
     # Chai2018 / Hu2019 take gamma from FP64 atomic sums, whose order varies
@@ -394,18 +405,22 @@ def test_tma_staging_matches_cp_async_bitwise(shape, fam, storage, lat):
     assert oa["vol_count"] == ob["vol_count"] and abs(oa["sum_phi"] / ob["sum_phi"] - 1) < 1e-12
 
 
-@pytest.mark.parametrize("shape,fam,tma", [((64, 11, 9), C.FAKHARI2017, 0), ((35, 12, 9), C.FAKHARI2017, 0),
-                                          ((64, 4, 9), C.FAKHARI2017, 0), ((64, 12, 9), C.LIANG2014, 0),
-                                          ((64, 12, 9), C.FAKHARI2017, 1)])
-def test_tma_staging_where_the_geometry_allows(shape, fam, tma):
-    """TMA staging is used for 3D domains with nx a multiple of 32 and ny a
-    multiple of the tile's 4 rows (at least 8), Allen-Cahn families; elsewhere
-    the step falls back to cp.async staging."""
+@pytest.mark.parametrize("shape,fam,storage,tma", [
+    ((64, 11, 9), C.FAKHARI2017, 0, 0), ((35, 12, 9), C.FAKHARI2017, 0, 0), ((64, 4, 9), C.FAKHARI2017, 0, 0),
+    ((64, 12, 9), C.LIANG2014, 0, 0), ((64, 12, 9), C.FAKHARI2017, 0, 1), ((64, 12, 9), C.FAKHARI2017, 1, 0)])
+def test_tma_staging_where_the_geometry_allows(shape, fam, storage, tma):
+    """By default TMA staging is used for FP32 storage on 3D domains with nx
+    a multiple of 32 and ny a multiple of the tile's 4 rows (at least 8),
+    Allen-Cahn families; 16-bit storage and other geometries use cp.async
+    staging. Mode 1 asks for TMA wherever the geometry allows it."""
     nx, ny, nz = shape
     P, phi, u = C.droplet_in_tgv_3d(nx=nx, ny=ny, nz=nz, R=3.0, W=2.5, family=fam)
-    s = make_sim(P, phi, u)
+    s = make_sim(P, phi, u, storage=storage)
     assert s.staging == tma
+    s.set_staging(1)
+    geometry = nx % 32 == 0 and ny % 4 == 0 and ny >= 8 and fam != C.LIANG2014
+    assert s.staging == int(geometry)
     s.set_staging(0)
     assert s.staging == 0
     with pytest.raises(pflb.PflbError):
-        s.set_staging(2)
+        s.set_staging(3)

@@ -51,7 +51,7 @@ class _Oracle:
 def hit48():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    L.start()
+    L.start(("turb",))
     P, phi32, u32, stats = L.turbulence_inputs()
     require_gpu()
     print("spun-up turbulence %d^3: Re_lambda %.1f, u' %.4f, eps %.3e, eta %.2f, A %.3e; "
@@ -120,15 +120,18 @@ def test_hit48_fp32_series_vs_oracle(hit48, We):
     assert drift_g <= 1e-6 and vs_g <= 1e-6
 
 
-STORAGE_SERIES_BOUND = {1: 5e-2, 2: 5e-2}
+# measured over 800 steps (stochastically rounded 16-bit stores): FP16 KE
+# 2.3e-4, V_count 1.1e-3, sum(phi) drift 1.1e-4; BF16 KE 2.0e-3, V_count
+# 4.9e-3, drift 6.9e-4 -- bounds with a factor 3 to 5
+STORAGE_SERIES_BOUND = {1: (5e-3, 5e-4), 2: (1.5e-2, 3e-3)}
 
 
 @pytest.mark.parametrize("storage", [1, 2], ids=["fp16", "bf16"])
 def test_hit48_16bit_series(hit48, storage):
     """FP16 / BF16 deviation storage on the same case (We = 5): the KE and
     volume series against the FP32 GPU run and against the FP64 oracle, and
-    the sum(phi) drift the 16-bit rounding causes; bounds are the measured
-    errors with margin."""
+    the sum(phi) drift of the stochastically rounded 16-bit stores; bounds
+    are the measured errors with margin."""
     We = 5.0
     P = hit48["P"][We]
     g32, _ = gpu_run(P, hit48["phi"], hit48["u"])
@@ -144,5 +147,6 @@ def test_hit48_16bit_series(hit48, storage):
           "over %d steps" % (name, ke_32.max(), vc_32.max(), ke_o.max(), vc_o.max(), drift, NSTEPS))
     record("series16", storage=name, ke_vs_fp32=float(ke_32.max()), vcount_vs_fp32=float(vc_32.max()),
            ke_vs_oracle=float(ke_o.max()), vcount_vs_oracle=float(vc_o.max()), sum_phi_drift=drift)
-    b = STORAGE_SERIES_BOUND[storage]
+    b, b_drift = STORAGE_SERIES_BOUND[storage]
     assert ke_o.max() <= b and vc_o.max() <= b
+    assert drift <= b_drift
