@@ -47,6 +47,19 @@ KERNEL_SOURCES = ["pflb_step.cuh", "pflb_common.cuh", "pflb_symsum.cuh", "pflb_a
                   "pflb_fam_fakhari.cu"]
 
 
+def _min_bytes_per_lu(fam, storage):
+    """Minimum bytes per lattice update of a pass-sequence family on D3Q19 +
+    D3Q7 (3D): its populations read and written once. Bao2024 (Cahn-Hilliard)
+    keeps all seven phase-field populations (its rest population carries
+    mass: 2 x 4 x (19 + 7) = 208 B); Liu2023 (hybrid Allen-Cahn) the six
+    moving ones and the phi u of the previous step for its time derivative
+    (2 x 4 x (19 + 6) + 2 x 4 x 3 = 224 B). None for the fused families,
+    whose counted bytes are already that minimum, and for 16-bit storage."""
+    if storage != 0:
+        return None
+    return {C.BAO2024: 208.0, C.LIU2023: 224.0}.get(fam)
+
+
 def _traffic(n):
     """DRAM bytes per launch of the FP32 step from the committed ncu record,
     or None when the record is for another size or the kernel sources have
@@ -598,6 +611,13 @@ def main():
                     "value": cells * args.steps * world / t3 / 1e9, "unit": "GLUPS", "bytes_per_lu": b3,
                     "roofline_frac": b3 * cells / (t3 / args.steps) / 1e9 / peak,
                     "ms_per_step": t3 / args.steps * 1e3, "time_vs_fakhari2017": t3 / t}
+                bmin = _min_bytes_per_lu(fam, storage)
+                if bmin is not None:
+                    # the pass sequences count every pass's reads and writes;
+                    # against the method's own minimum (populations once each
+                    # way, plus the fields it must carry between steps)
+                    fams[C.FAMILY_NAMES[fam]].update(
+                        min_bytes_per_lu=bmin, roofline_frac_vs_min=bmin * cells / (t3 / args.steps) / 1e9 / peak)
             variants["families_%s" % args.storage] = fams
             # The paper's own 3D hydrodynamics: D3Q27 with the MRT collision
             # (Sec. IV; rates of Reading R20), same workload and family.

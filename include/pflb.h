@@ -235,6 +235,20 @@ int pflb_set_staging(pflb_handle* h, int32_t mode);
  * PFLB_EINVAL for a NULL handle. */
 int pflb_get_staging(const pflb_handle* h);
 
+/* Failure-injection hook for tests of the bounded waits (the paper has no
+ * counterpart). With polls > 0, every block of each following TMA-staged
+ * step first waits on a shared-memory barrier that nothing completes, gives
+ * up after `polls` polls and reports a timed-out wait in that step's status;
+ * the step itself then runs unchanged. pflb_sync and pflb_observables turn
+ * that status into PFLB_ETIMEOUT, which, like every error but
+ * PFLB_EUNSTABLE, stays on the handle (pflb_step and pflb_init refuse
+ * further work; the handle can still be read and destroyed, and other
+ * handles are unaffected). polls = 0 switches the hook off; steps staged by
+ * cp.async have no waits and ignore it. PFLB_EINVAL for polls outside
+ * [0, 65536] or, with polls > 0, a handle whose next step is not
+ * TMA-staged (pflb_get_staging). */
+int pflb_inject_wait_timeout(pflb_handle* h, int32_t polls);
+
 /* Velocity set of a lattice in canonical order. which: 0 = phase field (g),
  * 1 = hydrodynamics (f: D2Q9 / D3Q19), 2 = the D3Q27 hydrodynamic lattice
  * (dim 3 only). q receives Q; e receives 3*Q ints (ex, ey, ez per

@@ -57,6 +57,7 @@ extern "C" int pflb_adjoint(pflb_handle* h, int64_t nsteps, int32_t checkpoint_e
   if (!h->initialized || h->step != 0)
     return handle_fail(h, PFLB_EINVAL, "pflb_adjoint starts from the state pflb_init made (step 0)");
   if (!(w->eps_v > 0.0)) return handle_fail(h, PFLB_EINVAL, "eps_v must be > 0");
+  const NvtxRange range("pflb_adjoint");
 
   const long long N = h->N;
   const int dim = h->dim, QG = h->QG, QF = h->QF;

@@ -235,6 +235,7 @@ StepArgs pflb::handle_step_args(const pflb_handle* h) {
   a.N = h->N;
   a.tma = (h->staging == 1 || (h->staging == 2 && h->storage == 0 && h->QF == 19)) ? h->tma[h->cur] : nullptr;
   a.seed = (unsigned)h->step;
+  a.test_wait_polls = h->test_wait_polls;
   return a;
 }
 
@@ -393,6 +394,7 @@ int pflb_init(pflb_handle* h, const float* phi0, const float* u0) {
 int pflb_step(pflb_handle* h, int64_t nsteps) {
   if (!h || nsteps < 0) return handle_fail(h, PFLB_EINVAL, "invalid argument");
   if (h->status != PFLB_OK && h->status != PFLB_EUNSTABLE) return h->status;
+  const NvtxRange range("pflb_step");
   for (int64_t i = 0; i < nsteps; ++i) {
     StepArgs a = handle_step_args(h);
     a.obs_slot = h->obs + (h->step % h->obs_cap);

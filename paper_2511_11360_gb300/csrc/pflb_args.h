@@ -46,6 +46,7 @@ struct StepArgs {
   float* work;            // Bao2024: phi, mu, p, u fields ((3 + d) x N); Liu2023: 6 x N
   const TmaMaps* tma = nullptr;  // host copy of this step's tensor maps (TMA staging), or null
   unsigned seed = 0u;     // step counter: seeds the stochastic rounding of 16-bit stores
+  int test_wait_polls = 0;  // > 0: TMA-staged blocks first run out a wait of this many polls (test hook)
 };
 
 struct InitArgs {

@@ -550,6 +550,7 @@ int pflb_batch_step(pflb_batch* b, int64_t nsteps) {
   if (!b) return PFLB_EINVAL;
   if (nsteps < 0) return bfail(b, PFLB_EINVAL, "nsteps must be >= 0");
   if (b->status != PFLB_OK && b->status != PFLB_EUNSTABLE) return b->status;
+  const NvtxRange range("pflb_batch_step");
   return step_impl(b, nsteps, b->use_graph);
 }
 

@@ -2,8 +2,19 @@
 // one domain and the helpers the batch entry points reuse.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>   // header-only NVTX v3 (no link dependency)
+
 #include "../../include/pflb.h"
 #include "pflb_args.h"
+
+// NVTX range over one C ABI call (a host-side range around the launches it
+// enqueues: profilers can filter kernels by it, e.g. ncu --nvtx).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct pflb_handle {
   pflb_params prm;
@@ -27,6 +38,7 @@ struct pflb_handle {
   int status = PFLB_OK;
   char err[512] = {0};
   pflb::TmaMaps* tma[2] = {nullptr, nullptr};  // tensor maps per g source buffer (TMA staging), or null
+  int test_wait_polls = 0;      // wait-timeout test hook (pflb_inject_wait_timeout)
   int staging = 2;              // 0 cp.async staging; 1 TMA where the geometry allows it; 2 TMA for FP32 D3Q19 only
 };
 

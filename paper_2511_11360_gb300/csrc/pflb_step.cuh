@@ -463,7 +463,9 @@ struct TileSmem {
   // 128 bytes of slack to align the dynamic base), then NST mbarriers.
   using TS = TmaStage<TB, (DIM == 3 && !CH) ? Lattices<DIM, LAT>::G::Q - 1 : Lattices<DIM, LAT>::G::Q,
                       Lattices<DIM, LAT>::F::Q, nsx<typename Lattices<DIM, LAT>::F>(), (int)sizeof(T), PAR>;
-  static constexpr int STAGE = TMA ? (NST * TS::BYTES + 128 + 8 * NST) / 4 : (STAGED ? NST * (FST + GST) : 0);
+  // TMA: the stages, 128 bytes of alignment slack, NST stage barriers and
+  // one barrier of the wait-timeout test hook
+  static constexpr int STAGE = TMA ? (NST * TS::BYTES + 128 + 8 * (NST + 1)) / 4 : (STAGED ? NST * (FST + GST) : 0);
   static_assert(!COOP || (FST % 4 == 0 && GST % 4 == 0), "16-byte aligned stages");
   static constexpr size_t BYTES = (size_t)(STAGE + PHI + MU) * sizeof(float);
 };
@@ -956,10 +958,17 @@ __device__ __forceinline__ void step_tile(const StepArgs& args, int a0, int b0, 
       }
     }
     if (tid == 0) {
-      for (int k = 0; k < NST; ++k) mbar_init(tbar + 8u * k, 1u);
+      for (int k = 0; k < NST + 1; ++k) mbar_init(tbar + 8u * k, 1u);
       mbar_init_fence();
     }
     __syncthreads();
+    if (args.test_wait_polls > 0) {
+      // Test hook for the bounded waits: wait on barrier NST, which no
+      // thread and no copy ever completes, give up after the given number
+      // of polls and report it as a timed-out wait; the step then proceeds
+      // unchanged (no copy is in flight yet).
+      if (!mbar_wait_bounded(tbar + 8u * NST, 0u, args.test_wait_polls)) obs.bad |= kStatusTimeout;
+    }
   }
   // Warp 0: the copies of g of plane cg and f of plane cf into stage s.
   auto tma_issue = [&](int cg, int cf, int s) {

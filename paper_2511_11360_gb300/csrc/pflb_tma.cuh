@@ -68,8 +68,8 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
   return ok != 0u;
 }
 // Wait for phase `parity` of the barrier; false if the poll limit ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
-  for (int i = 0; i < kTmaWaitPolls; ++i)
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity, int polls = kTmaWaitPolls) {
+  for (int i = 0; i < polls; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }

@@ -109,9 +109,22 @@ int handle_build_tma(pflb_handle* h) {
 
 }  // namespace pflb
 
+// Upper bound on the test hook's poll count (each poll of an mbarrier may
+// suspend the thread for a short, hardware-chosen time).
+static constexpr int kMaxTestWaitPolls = 1 << 16;
+
 int pflb_set_staging(pflb_handle* h, int32_t mode) {
   if (!h || mode < 0 || mode > 2) return pflb::handle_fail(h, PFLB_EINVAL, "staging mode must be 0, 1 or 2");
   h->staging = mode;
+  return PFLB_OK;
+}
+
+int pflb_inject_wait_timeout(pflb_handle* h, int32_t polls) {
+  if (!h || polls < 0 || polls > kMaxTestWaitPolls)
+    return pflb::handle_fail(h, PFLB_EINVAL, "polls must be in [0, %d]", kMaxTestWaitPolls);
+  if (polls > 0 && pflb_get_staging(h) != 1)
+    return pflb::handle_fail(h, PFLB_EINVAL, "the wait-timeout hook needs a TMA-staged step (pflb_get_staging)");
+  h->test_wait_polls = polls;
   return PFLB_OK;
 }
 

@@ -103,6 +103,7 @@ SIGNATURES = {
     "pflb_set_chunk": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "pflb_set_staging": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "pflb_get_staging": (ctypes.c_int, [ctypes.c_void_p]),
+    "pflb_inject_wait_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "pflb_lattice": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                     ctypes.c_void_p, ctypes.c_void_p]),
     "pflb_destroy": (ctypes.c_int, [ctypes.c_void_p]),
@@ -279,6 +280,11 @@ class Sim:
     def staging(self):
         """1 if the next step uses TMA staging, else 0."""
         return int(self.lib.pflb_get_staging(self.h))
+
+    def inject_wait_timeout(self, polls):
+        """Test hook: each block of the following TMA-staged steps runs out a
+        bounded wait of `polls` polls and reports PFLB_ETIMEOUT (0: off)."""
+        return self._check(self.lib.pflb_inject_wait_timeout(self.h, int(polls)))
 
     def bytes_per_update(self):
         return float(self.lib.pflb_bytes_per_update(self.h))

@@ -4,14 +4,14 @@ It serves callers that cannot allocate device memory (an application that
 owns all device memory through its own allocator, or a latency-bound loop
 that cannot afford the synchronisation cudaMalloc implies). Its scratch is a
 file-scope device array shared by every call; this file checks its sums
-against pflb_observables on the same state, and against plain FP64 sums of
-the same phi, on two calls in a row, on fields that span several partial
-records with a ragged last one, followed by a smaller field that uses fewer
-records (the array keeps the larger call's records; they must not be read).
-Sizes beyond the array are refused by the library, and buffers the library
-would read out of bounds are refused by the binding before any call.
-Collected last so a stop at the first failure has run every other test; it
-also passes alone.
+against pflb_observables on the same state, against plain FP64 sums of the
+same phi and against the oracle's observables of that phi, on two calls in a
+row, on fields that span several partial records with a ragged last one,
+followed by a smaller field that uses fewer records (the array keeps the
+larger call's records; they must not be read). Sizes beyond the array are
+refused by the library, and buffers the library would read out of bounds are
+refused by the binding before any call. Collected last so a stop at the
+first failure has run every other test; it also passes alone.
 """
 
 import numpy as np
@@ -19,6 +19,8 @@ import pytest
 
 from paper_2511_11360_gb300 import cases as C
 from paper_2511_11360_gb300 import pflb
+
+import oracle as O
 
 torch = pytest.importorskip("torch")
 
@@ -46,6 +48,27 @@ def _plain_sums(P, phi):
     return dict(sum_phi=float(phi.sum()), vol_smooth=float(frac.sum()),
                 vol_count=int(np.count_nonzero(phi.astype(np.float32) > phi0)),
                 phi_max=float(phi.max()), phi_min=float(phi.min()), centroid=cen)
+
+
+def _oracle_sums(P, phi):
+    """The oracle's observables of the FP32 phi: the FP64 oracle state
+    initialised at rest from phi (its phi = sum g is phi to FP64 round-off),
+    with the velocity-dependent entries dropped."""
+    phi = np.asarray(phi, dtype=np.float64)
+    u = np.zeros((P["dim"],) + phi.shape)
+    ob = O.observables(P, O.init_state(P, phi, u))
+    # cells whose count could flip under that round-off
+    ob["near_phi0"] = int(np.count_nonzero(np.abs(phi - 0.5 * (P["phi_H"] + P["phi_L"])) < 1e-12))
+    return ob
+
+
+def _check_oracle(got, want):
+    assert abs(got["sum_phi"] / want["sum_phi"] - 1) < 1e-6
+    assert abs(got["vol_smooth"] / want["vol_smooth"] - 1) < 1e-6
+    assert abs(got["vol_count"] - want["vol_count"]) <= want["near_phi0"]
+    assert abs(got["phi_max"] - want["phi_max"]) < 1e-12 and abs(got["phi_min"] - want["phi_min"]) < 1e-12
+    for k, c in enumerate(want["centroid"]):
+        assert abs(got["centroid"][k] - c) < 1e-4
 
 
 def _case(kind):
@@ -109,6 +132,7 @@ def test_static_sums_match_observables_twice(_gpu, kind):
         got = pflb.phase_sums_static(P, dphi, stream=stream)
         _check(got, want)
         _check(got, _plain_sums(P, dphi.cpu().numpy()))
+        _check_oracle(got, _oracle_sums(P, dphi.cpu().numpy()))
 
 
 @pytest.mark.gpu
