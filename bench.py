@@ -55,6 +55,7 @@ def _min_bytes_per_lu(fam, storage):
     moving ones and the phi u of the previous step for its time derivative
     (2 x 4 x (19 + 6) + 2 x 4 x 3 = 224 B). None for the fused families,
     whose counted bytes are already that minimum, and for 16-bit storage."""
+    from paper_2511_11360_gb300 import cases as C
     if storage != 0:
         return None
     return {C.BAO2024: 208.0, C.LIU2023: 224.0}.get(fam)

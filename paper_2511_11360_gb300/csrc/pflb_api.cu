@@ -346,7 +346,7 @@ int pflb_create(const pflb_params* params, void* cuda_stream, pflb_handle** out)
   if ((rc = alloc(&h->g[1], (size_t)h->QG * npad * h->elem + 16))) return rc;
   if ((rc = alloc(&h->f, (size_t)h->QF * npad * h->elem + 16))) return rc;
   if (fam_phiu(h->family) && (rc = alloc((void**)&h->phiu, (size_t)h->dim * h->N * sizeof(float)))) return rc;
-  if (h->family == PFLB_CH_BAO2024 && (rc = alloc((void**)&h->work, (size_t)(3 + h->dim) * h->N * sizeof(float))))
+  if (h->family == PFLB_CH_BAO2024 && (rc = alloc((void**)&h->work, (size_t)(4 + 2 * h->dim) * h->N * sizeof(float))))
     return rc;
   if (h->family == PFLB_HAC_LIU2023 && (rc = alloc((void**)&h->work, (size_t)6 * h->N * sizeof(float)))) return rc;
   if ((rc = alloc((void**)&h->obs, (size_t)(h->obs_cap + 1) * sizeof(DevObs)))) return rc;
@@ -548,8 +548,10 @@ double pflb_bytes_per_update(const pflb_handle* h) {
   if (h->family == PFLB_CH_BAO2024) {
     // the passes: g read for phi, phi and mu written and read by the mu,
     // macroscopic and collision passes, f read for u and p, u and p written
-    // and read (field words of 4 bytes)
-    b += 4.0 * (qg + 1) + 8.0 + 4.0 * h->QF + 8.0 + 4.0 * (h->dim + 1) + 4.0 * (3 + h->dim);
+    // and read, grad mu and div(M grad mu) written and read (field words of
+    // 4 bytes)
+    b += 4.0 * (qg + 1) + 8.0 + 4.0 * h->QF + 8.0 + 4.0 * (h->dim + 1) + 4.0 * (3 + h->dim) +
+         8.0 * (h->dim + 1);
   }
   if (h->family == PFLB_HAC_LIU2023) {
     // the passes: g read for phi*, phi* S(psi0) psi written; per

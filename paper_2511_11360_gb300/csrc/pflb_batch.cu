@@ -27,7 +27,7 @@ struct pflb_batch {
   int fam_n[kBatchFams] = {};
   int fgrid[kBatchFams] = {};       // persistent blocks of each family's kernel
   cudaStream_t fstream[kBatchFams] = {};   // branches of a step (the first family runs on the step's stream)
-  cudaEvent_t ev_fork = nullptr, ev_join[kBatchFams] = {};
+  cudaEvent_t ev_fork = nullptr, ev_gamma = nullptr, ev_join[kBatchFams] = {};
   int ggrid = 0;                   // blocks of the gamma pre-pass
   BatchTile* d_tiles = nullptr;
   int ntiles = 0;
@@ -200,20 +200,22 @@ int prepare(pflb_batch* b) {
 // One batched step using argument table k, on stream s: the gamma pre-pass,
 // then one kernel per family present, forked on the family streams after the
 // pre-pass and joined back into s (the same dependencies in a captured graph).
+// The nonlocal family whose kernel runs on the step's own stream (the first
+// of Chai2018, Hu2019 present), or -1.
+int first_nonlocal(const pflb_batch* b) {
+  if (b->fam_n[FAM_CHAI] > 0) return FAM_CHAI;
+  if (b->fam_n[FAM_HU] > 0) return FAM_HU;
+  return -1;
+}
+
 void launch_one(pflb_batch* b, int k, cudaStream_t s) {
   const int n = n_of(b);
-  if (b->ngent > 0) {
-    BatchGammaArgs ga;
-    ga.args = b->d_args + (size_t)k * n;
-    ga.ent = b->d_gent;
-    ga.nent = b->ngent;
-    ga.ninst = n;
-    batch_gamma(ga, b->ggrid, s);
-  }
-  bool first = true;
+  // One step as a fork / join over the families' kernels. Every branch
+  // starts after the previous step (the fork on s); the nonlocal families
+  // (Chai2018, Hu2019) also wait for the gamma pre-pass on s, while the
+  // local ones run beside it on their own streams.
   cudaEventRecord(b->ev_fork, s);
-  for (int f = 0; f < kBatchFams; ++f) {
-    if (b->fam_n[f] == 0) continue;
+  auto args_of = [&](int f) {
     BatchArgs ba;
     ba.args = b->d_args + (size_t)k * n;
     ba.tiles = b->d_tiles + b->fam_t0[f];
@@ -222,14 +224,38 @@ void launch_one(pflb_batch* b, int k, cudaStream_t s) {
     ba.chunk = b->cfg.chunk;
     ba.counter = b->d_counter + k * kBatchFams + f;
     ba.counter_next = b->d_counter + (1 - k) * kBatchFams + f;
-    cudaStream_t sf = first ? s : b->fstream[f];
-    if (!first) cudaStreamWaitEvent(sf, b->ev_fork, 0);
-    batch_step(b->cfg.tile_a, f, ba, b->fgrid[f], sf);
-    if (!first) {
-      cudaEventRecord(b->ev_join[f], sf);
-      cudaStreamWaitEvent(s, b->ev_join[f], 0);
+    return ba;
+  };
+  auto branch = [&](int f, cudaEvent_t after) {
+    cudaStream_t sf = b->fstream[f];
+    cudaStreamWaitEvent(sf, after, 0);
+    batch_step(b->cfg.tile_a, f, args_of(f), b->fgrid[f], sf);
+    cudaEventRecord(b->ev_join[f], sf);
+  };
+  for (int f = 0; f < kBatchFams; ++f)
+    if (b->fam_n[f] > 0 && f != FAM_CHAI && f != FAM_HU) branch(f, b->ev_fork);
+  if (b->ngent > 0) {
+    BatchGammaArgs ga;
+    ga.args = b->d_args + (size_t)k * n;
+    ga.ent = b->d_gent;
+    ga.nent = b->ngent;
+    ga.ninst = n;
+    batch_gamma(ga, b->ggrid, s);
+  }
+  cudaEventRecord(b->ev_gamma, s);
+  bool on_s = false;   // the first nonlocal family runs on s itself
+  for (int f : {FAM_CHAI, FAM_HU}) {
+    if (b->fam_n[f] == 0) continue;
+    if (!on_s) {
+      batch_step(b->cfg.tile_a, f, args_of(f), b->fgrid[f], s);
+      on_s = true;
+    } else {
+      branch(f, b->ev_gamma);
     }
-    first = false;
+  }
+  for (int f = 0; f < kBatchFams; ++f) {
+    const bool side = b->fam_n[f] > 0 && !((f == FAM_CHAI || f == FAM_HU) && f == first_nonlocal(b));
+    if (side) cudaStreamWaitEvent(s, b->ev_join[f], 0);
   }
 }
 
@@ -511,6 +537,7 @@ int pflb_batch_create(const pflb_params* params, int32_t n, void* cuda_stream, p
   BCU(b, cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
   BCU(b, cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
   BCU(b, cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+  BCU(b, cudaEventCreateWithFlags(&b->ev_gamma, cudaEventDisableTiming));
   for (int f = 0; f < kBatchFams; ++f) {
     BCU(b, cudaStreamCreateWithFlags(&b->fstream[f], cudaStreamNonBlocking));
     BCU(b, cudaEventCreateWithFlags(&b->ev_join[f], cudaEventDisableTiming));
@@ -680,6 +707,7 @@ int pflb_batch_destroy(pflb_batch* b) {
     if (b->ev_join[f]) cudaEventDestroy(b->ev_join[f]);
   }
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_gamma) cudaEventDestroy(b->ev_gamma);
   if (b->gstream) cudaStreamDestroy(b->gstream);
   cudaFree(b->d_tiles);
   cudaFree(b->d_gent);

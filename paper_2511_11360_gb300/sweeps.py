@@ -13,8 +13,8 @@ after the droplet is inserted, 10,000 steps, and three sweeps:
 
 with We = rho_H u_rms^2 (2R) / sigma, for Fakhari2017, Liang2018, Chai2018,
 Liu2023, Liang2014 and Bao2024. Each run records the droplet volume (the
-count of cells with phi > phi_0, Sec. IV A), phi_max and phi_min every
-`every` steps and whether the state stayed finite.
+count of cells with phi > phi_0, Sec. IV A), the kinetic energy, phi_max
+and phi_min every `every` steps and whether the state stayed finite.
 
 Differences from the paper, each forced by what is available here: its
 stochastic forcing (and the spun-up field it produced, Re_lambda = 42.3) is
@@ -102,7 +102,8 @@ def run_one(fam, s, n, R, u, u_prime, nu, A, steps, every, stream):
                lattice="D3Q27 MRT" if lat["lattice_f"] == 27 else "D3Q19 BGK", status=status, steps=done,
                seconds=secs, step=steps_rec, V_over_V0=(v[::every] / v[0]).round(6).tolist(),
                phi_max=[round(h["phi_max"], 6) for h in hist][::every],
-               phi_min=[round(h["phi_min"], 6) for h in hist][::every])
+               phi_min=[round(h["phi_min"], 6) for h in hist][::every],
+               ke_over_ke0=[round(h["ke"] / hist[0]["ke"], 6) for h in hist][::every])
     finite = [x for x in rec["V_over_V0"] if math.isfinite(x)]
     rec["final_V_over_V0"] = finite[-1] if finite and status == "stable" else None
     return rec
