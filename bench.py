@@ -229,15 +229,19 @@ def e2e_run(P, phi_host, u_host, steps, world):
     torch.cuda.synchronize()
     _barrier(world)
     t0 = time.perf_counter()
-    sim.init(phi_host, u_host)
+    sim.init(phi_host, u_host)            # returns after the upload and init kernel
+    ta = time.perf_counter()
     for _ in range(steps):
         sim.step(1)
-        sim.history(1)
+        sim.history(1)                    # synchronous read of the step's observables
+    tb = time.perf_counter()
     sim.fields(phi=out_phi)
     t1 = time.perf_counter()
     _barrier(world)
     sim.close()
-    return t1 - t0
+    # where the time went (host clock; each phase ends in a synchronisation)
+    split = {"init_upload_ms": (ta - t0) * 1e3, "steps_ms": (tb - ta) * 1e3, "fields_download_ms": (t1 - tb) * 1e3}
+    return t1 - t0, split
 
 
 def batched_variant(steps, warmup, peak, count=512):
@@ -648,11 +652,12 @@ def main():
     del phi, u
     torch.cuda.empty_cache()
     e2e_steps = max(args.steps // 2, 5)
-    te = _max_over_ranks(e2e_run(dict(P, storage=storage, obs_capacity=4), phi_h.numpy(), u_h.numpy(),
-                                 e2e_steps, world), world)
+    te, split = e2e_run(dict(P, storage=storage, obs_capacity=4), phi_h.numpy(), u_h.numpy(), e2e_steps, world)
+    te = _max_over_ranks(te, world)
     e2e = {"value": cells * e2e_steps * world / te / 1e9, "unit": "GLUPS",
            "h2d_bytes_per_step": int(4 * cells * 4 / e2e_steps),
-           "d2h_bytes_per_step": int(96 + 4 * cells / e2e_steps)}
+           "d2h_bytes_per_step": int(96 + 4 * cells / e2e_steps),
+           "steps": e2e_steps, "split": {k: round(v, 2) for k, v in split.items()}}
 
     if rank != 0:
         if world > 1:

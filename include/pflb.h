@@ -210,7 +210,9 @@ int64_t pflb_step_count(const pflb_handle* h);
 double pflb_bytes_per_update(const pflb_handle* h);
 
 /* Launch shape of the fused step: cells per block along the marching axis
- * (z in 3D, y in 2D), 0 = library default. */
+ * (z in 3D, y in 2D), 0 = library default (about eight blocks per SM,
+ * marches of 4 to 128 planes; TMA-staged steps march at most 32 planes on
+ * even AA steps). The state after a step does not depend on it. */
 int pflb_set_chunk(pflb_handle* h, int32_t chunk);
 
 /* How the fused 3D step stages each plane's populations in shared memory.

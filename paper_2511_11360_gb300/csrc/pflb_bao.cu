@@ -10,14 +10,10 @@
 //   1. phi = sum g                                   -> work[phi]
 //   2. mu = 4 beta (...) - kappa lap phi             -> work[mu]
 //   3. u (Eq. yang_u_update), p (Eq. yang_p_update)  -> work[u], work[p];
-//      grad mu and div(M grad mu)                     -> work[gmu], work[divJ];
 //      observables of the state
-//   4. collision of g and f with the stencils of phi, u, p and the flux
-//      terms of pass 3; streaming.
-// The work buffer holds (4 + 2d) fields: phi, mu, p, u_x, u_y[, u_z],
-// (d mu/dx_k)_k, div(M grad mu). Pass 3 forms the flux terms once (they need
-// the stencils of mu and M(phi)) and pass 4 reads them back: 8 (d + 1) bytes
-// per cell of traffic instead of the stencil arithmetic a second time. Every
+//   4. collision of g and f with the stencils of phi, mu, M(phi), u, p;
+//      streaming.
+// The work buffer holds (3 + d) fields: phi, mu, p, u_x, u_y[, u_z]. Every
 // pass walks the domain as (x, y) tiles marching in z (pflb_pass.cuh).
 #include "pflb_init.cuh"
 #include "pflb_pass.cuh"
@@ -98,8 +94,6 @@ __global__ void __launch_bounds__(kThreads) bao_macro_kernel(const StepArgs a, P
   const float* mu = a.work + a.N;
   float* pf = a.work + 2 * a.N;
   float* uf = a.work + 3 * a.N;
-  float* gmf = a.work + (3 + DIM) * a.N;
-  float* divf = a.work + (3 + 2 * DIM) * a.N;
   const float* fb = static_cast<const float*>(a.f);
   __shared__ double s_red[(kThreads / 32) * 10];
   if (a.obs_zero != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&
@@ -154,11 +148,7 @@ __global__ void __launch_bounds__(kThreads) bao_macro_kernel(const StepArgs a, P
     } else {
       pf[c] = p;
 #pragma unroll
-      for (int k = 0; k < DIM; ++k) {
-        uf[k * a.N + c] = u[k];
-        gmf[k * a.N + c] = gmu[k];
-      }
-      divf[c] = divJ;
+      for (int k = 0; k < DIM; ++k) uf[k * a.N + c] = u[k];
     }
     comp_add(obs.s_hi, obs.s_lo, pc);
     const float fr = (pc - P.phiL) * P.inv_dphi;
@@ -199,8 +189,6 @@ __global__ void __launch_bounds__(kThreads) bao_collide_kernel(const StepArgs a,
   const float* mu = a.work + a.N;
   const float* pf = a.work + 2 * a.N;
   const float* uf = a.work + 3 * a.N;
-  const float* gmf = a.work + (3 + DIM) * a.N;
-  const float* divf = a.work + (3 + 2 * DIM) * a.N;
   const float* gs = static_cast<const float*>(a.g_src);
   float* gd = static_cast<float*>(a.g_dst);
   float* fb = static_cast<float*>(a.f);
@@ -222,10 +210,8 @@ __global__ void __launch_bounds__(kThreads) bao_collide_kernel(const StepArgs a,
     gather<DIM, LS>(phi, cl, vp);
     gather<DIM, LS>(pf, cl, vpr);
     const float pc = vp[0], p = vpr[0], muc = mu[c];
-    float gmu[DIM];
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) gmu[k] = gmf[k * a.N + c];
-    const float divJ = divf[c];
+    float gmu[DIM], divJ;
+    bao_flux<DIM>(P, vp, mu, cl, pc, gmu, divJ);
     const float rho = P.rhoL + P.drho_dphi * (pc - P.phiL);
     const float nu = viscosity(P, pc, rho);
     const float A_lks = (1.0f / itp) - 0.5f - bao_M(P, pc) * 3.0f / P.eta;   // Eq. (bao_Mphi)

@@ -26,7 +26,7 @@ struct pflb_handle {
   void* g[2] = {nullptr, nullptr};
   void* f = nullptr;
   float* phiu = nullptr;
-  float* work = nullptr;        // work fields: Bao2024 (4 + 2d) x N, Liu2023 6 x N
+  float* work = nullptr;        // work fields: Bao2024 (3 + d) x N, Liu2023 6 x N
   pflb::DevObs* obs = nullptr;  // ring of obs_cap slots + 1 slot for read-only passes
   int obs_cap = 2;
   double* gamma_acc = nullptr;  // 3 pairs: step ring (2) + read-only pass (1)

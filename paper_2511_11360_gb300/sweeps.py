@@ -19,8 +19,10 @@ and phi_min every `every` steps and whether the state stayed finite.
 Differences from the paper, each forced by what is available here: its
 stochastic forcing (and the spun-up field it produced, Re_lambda = 42.3) is
 replaced by the linear forcing A rho u from the seeded solenoidal field of
-cases.py, spun up single-phase through the library; Liu2023 and Bao2024 run
-on D3Q19 with BGK collision (their pass sequences have no D3Q27 form).
+cases.py, spun up single-phase through the library with A adjusted until the
+kinetic energy holds (initial u' 0.015, Re_lambda ~ 40 at nu = 0.006), then
+fixed for the droplet runs; Liu2023 and Bao2024 run on D3Q19 with BGK
+collision (their pass sequences have no D3Q27 form).
 
     python -m paper_2511_11360_gb300.sweeps --out sweeps.json [--n 256] [--steps 10000]
 """
@@ -51,21 +53,32 @@ def sweep_sets():
     return out
 
 
-def spin_up(n, nu, A, steps, stream, u_rms=0.04, seed=C.DEFAULT_SEED):
+def spin_up(n, nu, A, steps, stream, u_rms=0.015, seed=C.DEFAULT_SEED, every=500):
     """Single-phase turbulence: the seeded solenoidal field driven by linear
-    forcing A u for `steps` steps (D3Q27, MRT, FP32). Returns the velocity
-    field (device tensor) and its rms per component."""
+    forcing A u (D3Q27, MRT, FP32), with A adjusted every `every` steps so
+    that the kinetic energy stops growing or decaying: the net rate r of the
+    last block (KE ~ exp(r t), r = 2A - eps/k) gives A <- A - r/2, and the
+    next block restarts from the current velocity. Returns the velocity
+    field (device tensor), its rms per component, the final A and the
+    (u', A) of every block."""
     import torch
     u = C.solenoidal_field_torch(n, u_rms=u_rms, seed=seed, device="cuda")
-    P = C.params(dim=3, nx=n, ny=n, nz=n, family=C.FAKHARI2017, rho_H=1.0, rho_L=1.0, nu_H=nu, nu_L=nu,
-                 sigma=0.0, W=4.0, M=0.01, lundgren_A=A, lattice_f=27, collision=1, obs_capacity=4)
-    s = pflb.Sim(P, stream=stream)
-    s.init(torch.zeros((n, n, n), device="cuda"), u)
-    s.step(steps)
-    s.fields(u=u)
-    ke = s.observables()["ke"]
-    s.close()
-    return u, math.sqrt(2.0 * ke / (3.0 * n ** 3))
+    phi = torch.zeros((n, n, n), device="cuda")
+    trace = []
+    for _ in range(max(1, steps // every)):
+        P = C.params(dim=3, nx=n, ny=n, nz=n, family=C.FAKHARI2017, rho_H=1.0, rho_L=1.0, nu_H=nu, nu_L=nu,
+                     sigma=0.0, W=4.0, M=0.01, lundgren_A=A, lattice_f=27, collision=1, obs_capacity=every + 8)
+        s = pflb.Sim(P, stream=stream)
+        s.init(phi, u)
+        s.step(every)
+        hist = s.history(every)
+        s.fields(u=u)
+        s.close()
+        k0, k1 = hist[every // 2]["ke"], hist[-1]["ke"]   # second half: past the restart transient
+        r = math.log(k1 / k0) / (hist[-1]["step"] - hist[every // 2]["step"])
+        trace.append((math.sqrt(2.0 * k1 / (3.0 * n ** 3)), A))
+        A = max(A - 0.5 * r, 0.0)
+    return u, trace[-1][0], A, trace
 
 
 def droplet(n, R, xi):
@@ -118,9 +131,12 @@ def main(argv=None):
     ap.add_argument("--spin", type=int, default=5000)
     ap.add_argument("--every", type=int, default=100)
     ap.add_argument("--nu", type=float, default=0.006)
+    ap.add_argument("--urms", type=float, default=0.015,
+                    help="rms velocity of the initial field; with the default A, Re_lambda = u' (5/(A nu))^(1/2) "
+                         "is about 42 at nu = 0.006, n = 256, the paper's turbulence")
     ap.add_argument("--A", type=float, default=None,
-                    help="linear forcing coefficient (default u'/(3 l) with l = 0.19 n, the integral scale "
-                         "linear forcing settles at)")
+                    help="initial linear forcing coefficient of the spin-up, adjusted to hold the energy "
+                         "(default urms/(3 l) with l = 0.19 n, the integral scale linear forcing settles at)")
     ap.add_argument("--families", default=",".join(C.FAMILY_NAMES[f] for f in FAMILIES))
     ap.add_argument("--out", default="sweeps.json")
     args = ap.parse_args(argv)
@@ -129,8 +145,12 @@ def main(argv=None):
     pflb.load_library()
     stream = torch.cuda.current_stream()
     n = args.n
-    A = args.A if args.A is not None else 0.04 / (3.0 * 0.19 * n)
-    u, u_prime = spin_up(n, args.nu, A, args.spin, stream)
+    A0 = args.A if args.A is not None else args.urms / (3.0 * 0.19 * n)
+    u, u_prime, A, trace = spin_up(n, args.nu, A0, args.spin, stream, u_rms=args.urms)
+    # stationary linear forcing: eps = 3 A u'^2, Taylor microscale (15 nu u'^2 / eps)^(1/2)
+    re_lambda = u_prime * math.sqrt(5.0 / (A * args.nu))
+    print("spin-up (u', A) per block: %s; A = %.3e, u' = %.5f, Re_lambda %.1f" % (
+        ", ".join("(%.5f, %.2e)" % t for t in trace), A, u_prime, re_lambda), flush=True)
     names = {v: k for k, v in C.FAMILY_NAMES.items()}
     fams = [names[f] for f in args.families.split(",")]
     runs = []
@@ -144,8 +164,8 @@ def main(argv=None):
                 rec["family"], s["rho"], s["We"], s["xi"], rec["status"], rec["final_V_over_V0"], rec["seconds"]),
                 flush=True)
     out = dict(n=n, R=args.R, steps=args.steps, nu=args.nu, M=0.01, A=A, spin_up_steps=args.spin,
-               u_prime=u_prime, forcing="linear A rho u (the paper's stochastic forcing is not available)",
-               runs=runs)
+               u_prime=u_prime, spin_up_u_prime_A=trace, re_lambda=re_lambda,
+               forcing="linear A rho u (the paper's stochastic forcing is not available)", runs=runs)
     with open(args.out, "w") as fh:
         json.dump(out, fh)
     return 0
