@@ -60,9 +60,12 @@ int default_chunk(const pflb_handle* h, int parity, bool tma) {
   if (c > 128) c = 128;
   // TMA-staged steps: the even AA step (f read and written at the own cell)
   // runs faster in short marches, 4.66 -> 4.09 ms from 128 to 32 planes at
-  // 512^3, while the odd step (f from and to the neighbours) runs slower in
-  // them (5.40 -> 5.55 ms): 32 planes on even steps, the default on odd ones.
-  if (tma && parity == 0 && c > 32) c = 32;
+  // 512^3 (Fakhari2017; Chai2018 5.17 -> 4.57), while the odd step (f from
+  // and to the neighbours) runs slower in them (5.40 -> 5.55 ms): 32 planes
+  // on even steps, the default on odd ones. Liang2018, which also carries
+  // phi*u, gains nothing from short marches (5.34 -> 5.43 ms) and keeps the
+  // default.
+  if (tma && parity == 0 && !fam_phiu(h->family) && c > 32) c = 32;
   if (c > NC) c = NC;
   return (int)c;
 }
