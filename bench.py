@@ -578,7 +578,7 @@ def main():
         # tensor copies or per-thread cp.async), identical results
         s1 = pflb.Sim(dict(P, storage=storage, obs_capacity=4), stream=torch.cuda.current_stream())
         s1.init(phi, u)
-        s1.set_staging(0 if sim.staging == 1 else 1)
+        s1.set_staging(0 if staging == "tma" else 1)
         other = "tma" if s1.staging == 1 else "cp.async"
         if other != staging:
             t1 = _max_over_ranks(time_steps(s1, args.steps, args.warmup, world), world)
