@@ -224,17 +224,19 @@ int pflb_set_chunk(pflb_handle* h, int32_t chunk);
  * Hu2019 or Liang2018. cp.async staging: per-thread asynchronous copies.
  *   mode 0: cp.async staging everywhere;
  *   mode 1: TMA staging where available;
- *   mode 2 (the default): TMA staging for FP32 storage on D3Q19 where
- *           available, cp.async for the 16-bit forms (which are bound by
- *           instruction issue, where the per-thread barrier waits cost more
- *           than the copies they replace) and for D3Q27 (measured slower
- *           with TMA at three blocks per SM).
+ *   mode 2 (the default): TMA staging where available and measured
+ *           faster: FP32 storage on D3Q19 (both AA parities) and on the
+ *           even AA steps of D3Q27; cp.async on the odd D3Q27 steps (27
+ *           shifted boxes per plane at three blocks per SM measured slower)
+ *           and for the 16-bit forms (bound by instruction issue, where the
+ *           per-thread barrier waits cost more than the copies they
+ *           replace).
  * Both stagings compute bit-identical populations. PFLB_EINVAL for another
  * mode. */
 int pflb_set_staging(pflb_handle* h, int32_t mode);
 
-/* 1 if the next step of h uses TMA staging, 0 if it uses cp.async staging,
- * PFLB_EINVAL for a NULL handle. */
+/* 1 if the next step of h (its AA parity included) uses TMA staging, 0 if
+ * it uses cp.async staging, PFLB_EINVAL for a NULL handle. */
 int pflb_get_staging(const pflb_handle* h);
 
 /* Failure-injection hook for tests of the bounded waits (the paper has no

@@ -39,7 +39,7 @@ struct pflb_handle {
   char err[512] = {0};
   pflb::TmaMaps* tma[2] = {nullptr, nullptr};  // tensor maps per g source buffer (TMA staging), or null
   int test_wait_polls = 0;      // wait-timeout test hook (pflb_inject_wait_timeout)
-  int staging = 2;              // 0 cp.async staging; 1 TMA where the geometry allows it; 2 TMA for FP32 D3Q19 only
+  int staging = 2;              // 0 cp.async staging; 1 TMA where the geometry allows it; 2 TMA where it measured faster
 };
 
 namespace pflb {
@@ -58,6 +58,9 @@ void obs_to_host(const DevObs& d, long long step, pflb_obs* o);
 // tensor maps of its arrays (returns 1 when built; 0 leaves the cp.async path).
 bool handle_tma_eligible(const pflb_handle* h);
 int handle_build_tma(pflb_handle* h);
+// Whether a step of the given AA parity is staged by TMA under the handle's
+// staging mode (pflb_set_staging), given that its tensor maps were built.
+bool handle_tma_step(const pflb_handle* h, int parity);
 // Records a message and a sticky status on h; returns code.
 int handle_fail(pflb_handle* h, int code, const char* fmt, ...);
 

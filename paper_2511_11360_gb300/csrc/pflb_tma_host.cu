@@ -107,6 +107,18 @@ int handle_build_tma(pflb_handle* h) {
   return 1;
 }
 
+// Staging of a step of the given AA parity. Mode 2 (the default) takes TMA
+// where it measured faster at 512^3: FP32 D3Q19 on both parities (4.10 /
+// 5.39 ms against 5.06 / 5.57 with cp.async), FP32 D3Q27 on even steps
+// (5.49 against 6.63 ms; odd: 9.42 against 7.77); the 16-bit forms keep
+// cp.async (issue-bound: FP16 even 3.99 against 3.93 ms, odd 5.92 against
+// 4.58).
+bool handle_tma_step(const pflb_handle* h, int parity) {
+  if (h->staging == 1) return true;
+  if (h->staging != 2 || h->storage != 0) return false;
+  return h->QF == 19 || (h->QF == 27 && parity == 0);
+}
+
 }  // namespace pflb
 
 // Upper bound on the test hook's poll count (each poll of an mbarrier may
@@ -130,6 +142,5 @@ int pflb_inject_wait_timeout(pflb_handle* h, int32_t polls) {
 
 int pflb_get_staging(const pflb_handle* h) {
   if (!h) return PFLB_EINVAL;
-  const bool tma = h->staging == 1 || (h->staging == 2 && h->storage == 0 && h->QF == 19);
-  return (tma && h->tma[h->cur] != nullptr) ? 1 : 0;
+  return (pflb::handle_tma_step(h, (int)(h->step & 1)) && h->tma[h->cur] != nullptr) ? 1 : 0;
 }

@@ -273,12 +273,12 @@ class Sim:
 
     def set_staging(self, mode):
         """0: cp.async staging; 1: TMA where the geometry allows it; 2 (default):
-        TMA for FP32 storage on D3Q19 only."""
+        TMA where it measured faster (FP32 D3Q19; even steps of FP32 D3Q27)."""
         return self._check(self.lib.pflb_set_staging(self.h, int(mode)))
 
     @property
     def staging(self):
-        """1 if the next step uses TMA staging, else 0."""
+        """1 if the next step (its AA parity included) uses TMA staging, else 0."""
         return int(self.lib.pflb_get_staging(self.h))
 
     def inject_wait_timeout(self, polls):

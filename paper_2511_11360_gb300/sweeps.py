@@ -20,8 +20,8 @@ Differences from the paper, each forced by what is available here: its
 stochastic forcing (and the spun-up field it produced, Re_lambda = 42.3) is
 replaced by the linear forcing A rho u from the seeded solenoidal field of
 cases.py, spun up single-phase through the library with A adjusted until the
-kinetic energy holds (initial u' 0.015, Re_lambda ~ 40 at nu = 0.006), then
-fixed for the droplet runs; Liu2023 and Bao2024 run on D3Q19 with BGK
+kinetic energy holds (initial u' 0.015, 20,000 steps, about five large-eddy
+turnovers), then fixed for the droplet runs; Liu2023 and Bao2024 run on D3Q19 with BGK
 collision (their pass sequences have no D3Q27 form).
 
     python -m paper_2511_11360_gb300.sweeps --out sweeps.json [--n 256] [--steps 10000]
@@ -128,7 +128,9 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--R", type=float, default=30.0)
     ap.add_argument("--steps", type=int, default=10000)
-    ap.add_argument("--spin", type=int, default=5000)
+    ap.add_argument("--spin", type=int, default=20000,
+                    help="spin-up steps, in ten blocks between which the forcing coefficient is adjusted "
+                         "(about five large-eddy turnovers at the defaults)")
     ap.add_argument("--every", type=int, default=100)
     ap.add_argument("--nu", type=float, default=0.006)
     ap.add_argument("--urms", type=float, default=0.015,
@@ -146,7 +148,8 @@ def main(argv=None):
     stream = torch.cuda.current_stream()
     n = args.n
     A0 = args.A if args.A is not None else args.urms / (3.0 * 0.19 * n)
-    u, u_prime, A, trace = spin_up(n, args.nu, A0, args.spin, stream, u_rms=args.urms)
+    u, u_prime, A, trace = spin_up(n, args.nu, A0, args.spin, stream, u_rms=args.urms,
+                                   every=max(100, args.spin // 10))
     # stationary linear forcing: eps = 3 A u'^2, Taylor microscale (15 nu u'^2 / eps)^(1/2)
     re_lambda = u_prime * math.sqrt(5.0 / (A * args.nu))
     print("spin-up (u', A) per block: %s; A = %.3e, u' = %.5f, Re_lambda %.1f" % (
