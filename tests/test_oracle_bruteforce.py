@@ -1,6 +1,6 @@
-"""Brute-force pin of the FP64 oracle (north_star: "brute force on 8x8
-grids"): the oracle's vectorised numpy step against a literal per-cell,
-per-equation transcription in 30-digit arithmetic (tests/bruteforce_pflb.py,
+"""Brute-force pin of the FP64 oracle on 8x8 grids: the oracle's vectorised
+numpy step against a literal per-cell, per-equation transcription in
+30-digit arithmetic (tests/bruteforce_pflb.py,
 which shares no code with the oracle), over 10 steps from the same inputs,
 for every family, in 2D (periodic; moving walls with gravity and the four
 viscosity interpolations), and in 3D on 4^3 (D3Q19 + D3Q7; D3Q27 with BGK and
