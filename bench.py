@@ -520,6 +520,8 @@ def main():
     ap.add_argument("--no-families", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-weber", action="store_true")
+    ap.add_argument("--batched-count", type=int, default=512,
+                    help="domains of the batched sweep variant (the configuration's 512; fewer for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -640,7 +642,8 @@ def main():
         if not args.no_weber:
             variants["weber_series_%d" % n] = weber_series_variant(n=n)
         if not args.no_batched:
-            variants["batched_2d_shear_512"] = batched_variant(args.steps, args.warmup, peak)
+            variants["batched_2d_shear_%d" % args.batched_count] = batched_variant(args.steps, args.warmup, peak,
+                                                                                  count=args.batched_count)
         if not args.no_adjoint:
             variants["adjoint_tgv_128"] = adjoint_variant()
 
